@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Throughput of the scattered-field PIC step (arXiv 2310.11393) on GB300.
+
+One step = push + incident-field evaluation + gather + Boris + Esirkepov deposit for every
+macro-electron, the particle re-sort by tile, and the Yee update of the scattered field.
+Default workload: the 2D tightly focused LP case (1024 x 1024 cells, dx = lambda/32, LP pulse
+w0 = lambda, a0 = 10, 5 fs, 512 x 512-cell slab at 0.05 n_c with 8 ppc = 2 097 152 electrons).
+Metric: particle-pushes/s (each push includes the incident-field evaluation and the deposit).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2d|3d|1d]
+
+N > 1 (torchrun, one process per GPU): every rank advances its own replica of the workload
+(independent simulations: no data-path collective), timing is max over ranks and the value
+sums all ranks' pushes (weak scaling).  --impl reference times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "particle-pushes/s incl. incident-field eval+deposit"
+UNIT = "pushes/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d"])
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    return {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp}[name]()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def flops_per_push(w):
+    """Algorithmic FP32 operations of one push of the 2D/3D LP/RP path (counted from the formulas
+    the kernel evaluates; an FMA counts 2, a transcendental call counts 1)."""
+    D = w.dim
+    gather = 6 * (2 * 3 ** D) + D * 2 * 8                      # 3^D-point stencils, shape weights
+    boris = 60
+    deposit = {1: 40, 2: 220, 3: 1100}[D]
+    incident = {synth.BEAM_LP: 560, synth.BEAM_RP: 540, synth.BEAM_PLANE: 20}.get(w.beam, 0)
+    move = 10 * D
+    return gather + boris + deposit + incident + move
+
+
+def bytes_per_push(w):
+    """Algorithmic HBM bytes of one push: particle state read (cell, offsets, momenta, weight)
+    and written (cell, offsets, momenta), plus the field and current grid traffic shared by
+    the ppc particles of a cell (E, B read once; J read-modify-write once)."""
+    es = 4 if w.precision == synth.FP32 else 8
+    part = (4 + w.dim * es + 3 * es + es) + (4 + w.dim * es + 3 * es)
+    grid = (6 * es + 2 * 3 * es) / max(w.ppc, 1)
+    return part + grid
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2310_11393_gb300 import _build, pic
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload(args.workload)
+    cfg = pic.config_from(w)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    alloc = pic.torch_allocator(local_rank)
+    sim = pic.Simulation(cfg, allocator=alloc, stream=stream)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    n_a = sim.info().n_alive
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream(dev))
+    sim.step(args.steps)
+    e1.record(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) * 1e-3
+    clk = clocks.stop()
+    n_b = sim.info().n_alive
+    pushes = 0.5 * (n_a + n_b) * args.steps
+    t_max = secs
+    tot_pushes = pushes
+    if world > 1:
+        t = torch.tensor([secs], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        p = torch.tensor([pushes], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(p)
+        tot_pushes = float(p.item())
+        torch.distributed.barrier()
+    # live per-kernel timing of the same workload (events between the kernels of a step)
+    prof = pic.pic_profile_step(sim.h, args.profile_steps, stream)
+    n_c = sim.info().n_alive
+    push_s = prof[0] / args.profile_steps
+    yee_s = prof[3] / args.profile_steps
+    info = sim.info()
+    sim.close()
+
+    hbm, sm_max, src = peaks()
+    npush = 0.5 * (n_b + n_c)
+    fl = flops_per_push(w) * npush
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    alu_frac = fl / push_s / 1e12 / fp32_peak
+    by = bytes_per_push(w) * npush
+    hbm_frac = by / push_s / 1e9 / hbm
+    es = 4 if w.precision == synth.FP32 else 8
+    cells = w.n_cells
+    yee_bytes = cells * (9 * es + 6 * es + 3 * es)           # read E, B, J; write E, B; clear J
+    roof = {"bound": "alu", "achieved": round(fl / push_s / 1e12, 3), "peak": round(fp32_peak, 2),
+            "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": None,
+            "kernel": "k_push<%d,%s>" % (w.dim, "float" if es == 4 else "double"),
+            "peak_source": f"SM count x FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
+            "push_ms": round(push_s * 1e3, 4),
+            "hbm_view": {"achieved_gbs": round(by / push_s / 1e9, 1), "peak_gbs": hbm, "frac": round(hbm_frac, 4),
+                         "bytes_per_push": round(bytes_per_push(w), 2)},
+            "yee": {"ms": round(yee_s * 1e3, 4), "achieved_gbs": round(yee_bytes / yee_s / 1e9, 1),
+                    "frac_of_hbm": round(yee_bytes / yee_s / 1e9 / hbm, 4), "bytes_per_cell": 18 * es},
+            "phases_ms": [round(x / args.profile_steps * 1e3, 4) for x in prof]}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, w, pic, torch, dev, stream, alloc)
+    out = {"metric": METRIC, "value": tot_pushes / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if es == 4 else "f64", "data": "synthetic",
+           "config": {"workload": w.name, "dim": w.dim, "grid": list(w.n[: w.dim]), "particles": w.n_particles,
+                      "ppc": w.ppc, "beam": {1: "plane", 2: "LP", 3: "RP"}[w.beam],
+                      "precision": "fp32 body, fp64 phase" if es == 4 else "fp64",
+                      "cell_updates_per_s": cells * args.steps * world / t_max,
+                      "l2": "inputs larger than L2 (device state %.2f GB > 129 MB)" % (info.params.device_bytes / 1e9),
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "roofline": roof, "clocks": clk, "gpu_launches": 5 * args.steps, "e2e": e2e}
+    return out
+
+
+def run_e2e(args, w, pic, torch, dev, stream, alloc):
+    """Through the C-ABI with HOST buffers: the initial particle state goes host -> device, the
+    steps run, the energies and every particle's state come back device -> host."""
+    x, u, wt, ids = synth.slab_particles(w)
+    cfg = pic.config_from(w)
+    sim = pic.Simulation(cfg, allocator=alloc, stream=stream)
+    n = len(ids)
+    es = 4 if w.precision == synth.FP32 else 8
+    h2d = n * (4 + 4 + w.dim * es + 3 * es + es)
+    d2h = n * (4 + 4 + w.dim * es + 3 * es + es) + 64
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_particles(x, u, wt, ids)
+    sim.step(args.steps)
+    en = sim.energies()
+    parts = sim.particles()
+    t1 = time.perf_counter()
+    n_end = len(parts["id"])
+    sim.close()
+    pushes = 0.5 * (n + n_end) * args.steps
+    return {"value": pushes / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d / args.steps),
+            "d2h_bytes_per_step": int(d2h / args.steps), "seconds": t1 - t0,
+            "energies": [float(v) for v in en[:4]]}
+
+
+def cpu_baseline(w, nsteps):
+    """The oracle as it stands, single-threaded, on the full workload for nsteps steps."""
+    import oracle
+
+    sim = oracle.Sim(oracle.config_from(w))
+    n0 = sim.num_particles()
+    t0 = time.perf_counter()
+    sim.step(nsteps)
+    t1 = time.perf_counter()
+    n1 = sim.num_particles()
+    pushes = 0.5 * (n0 + n1) * nsteps
+    return {"value": pushes / (t1 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full {w.name} workload ({n0} electrons), {nsteps} steps from t = 0, FP64, 1 thread",
+            "seconds": t1 - t0}
+
+
+def run_reference(args, rank, world):
+    w = workload(args.workload)
+    import oracle
+
+    oracle.build()
+    sim = oracle.Sim(oracle.config_from(w))
+    sim.step(args.warmup)
+    n0 = sim.num_particles()
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    t1 = time.perf_counter()
+    n1 = sim.num_particles()
+    v = 0.5 * (n0 + n1) * args.steps / (t1 - t0)
+    cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"full {w.name} workload, {args.steps} steps after {args.warmup} warm-up steps, FP64, 1 thread"}
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": (t1 - t0) / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "dim": w.dim, "grid": list(w.n[: w.dim]), "particles": w.n_particles},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(workload(args.workload), 4) if world == 1 else None
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * pic.h -- C-ABI of the GB300 (sm_103a) scattered-field particle-in-cell library.
+ *
+ * The library advances the scattered-field PIC cycle of Lytova et al. (arXiv
+ * 2310.11393), Sec. 2 (the text after Eq. "scatt_field"): every macro-electron
+ * gathers the grid-held scattered field (order-2 shapes, Sec. 3.1), adds the
+ * closed-form incident field evaluated at its own position and time (plane wave
+ * of Sec. 3.1; the tightly focused LP pulse of Sec. 4.1, Eqs. components,
+ * phasor, poisson, poisson_dstr; the RP pulse generated by the Hertz vector
+ * Psi z^ of the same Eq. phasor), takes a relativistic Boris push of the Lorentz
+ * force in Eq. (vlasov), deposits an Esirkepov charge-conserving current, and
+ * then the Yee scheme advances the scattered field only (Eqs. MAmper,
+ * MFaraday).  Units are those of Table "tab:units": c = 1, omega = k = 1,
+ * lengths in lambda/2pi, electron charge -1, mass 1, densities in n_c.
+ *
+ * Conventions common to every entry point
+ *   - All calls return a pic_status; nothing aborts the process.  A failing call
+ *     records a message readable with pic_last_error().
+ *   - Pointers documented as HOST point to host memory owned by the caller and
+ *     are not retained after the call returns.  DEVICE state is owned by the
+ *     pic_sim and released by pic_destroy().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls documented as asynchronous only enqueue work; errors found
+ *     on the device (status word) surface at the next synchronous call.
+ *   - Grid geometry: axis x (the propagation axis of every beam), then y, then z;
+ *     `dim` resolved axes.  Node i of an axis sits at x = i*dx, i = 0..n; a field
+ *     component staggered along an axis (Yee: E_c, J_c along c; B_c along the two
+ *     other axes) has point i at (i + 1/2)*dx.
+ *   - Field boundaries: first-order Mur absorbing faces.  Particles closer than
+ *     `remove_margin` cells to a face leave the box (recorded as exits).
+ *   - Thread safety: one pic_sim must not be used by two host threads at once.
+ */
+#ifndef SFFPIC_PIC_H
+#define SFFPIC_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = -1,      /* invalid argument or configuration */
+    PIC_ENOMEM = -2,      /* device or host allocation failed */
+    PIC_ECUDA = -3,       /* a CUDA runtime/driver call failed (message has the CUDA error) */
+    PIC_ETIMEOUT = -4,    /* a bounded device wait gave up (status word bit PIC_FLAG_TIMEOUT) */
+    PIC_ENAN = -5,        /* a non-finite value was found by a diagnostic */
+    PIC_EBUSY = -6,       /* result not ready (serving) */
+    PIC_ECAPACITY = -7,   /* a fixed-capacity buffer overflowed (exits, particles, admission) */
+    PIC_ENODEV = -8,      /* no CUDA device of compute capability 10.3 available */
+    PIC_ENOTFOUND = -9    /* unknown ticket / handle */
+} pic_status;
+
+enum { PIC_BEAM_NONE = 0, PIC_BEAM_PLANE = 1, PIC_BEAM_LP = 2, PIC_BEAM_RP = 3, PIC_BEAM_UNIFORM = 4 };
+enum { PIC_ENV_SIN2 = 0, PIC_ENV_GAUSS = 1 };
+/* PIC_FP64: every quantity in double precision.
+ * PIC_FP32: particles, fields and the incident-field body in single precision; the
+ * incident-field phase (t -/+ x against the focal point / reference plane) and
+ * the particle coordinate it needs are formed in double precision first. */
+enum { PIC_FP64 = 0, PIC_FP32 = 1 };
+
+/* device status word bits (pic_info.status) */
+enum {
+    PIC_FLAG_TIMEOUT = 1u << 0,      /* an mbarrier wait exceeded its iteration bound */
+    PIC_FLAG_CFL = 1u << 1,          /* a particle moved more than one cell in a step (removed) */
+    PIC_FLAG_EXIT_OVERFLOW = 1u << 2 /* exit records beyond max_exits were dropped */
+};
+
+typedef struct {
+    int32_t dim;             /* 1, 2 or 3 */
+    int32_t n[3];            /* cells per axis (unused axes: 1) */
+    double dx;               /* cell size, code units (lambda/2pi) */
+    double dt;               /* time step; <= 0: cfl*dx/sqrt(dim) */
+    double cfl;              /* used when dt <= 0; must keep dt < dx/sqrt(dim) */
+    int32_t precision;       /* PIC_FP64 or PIC_FP32 */
+    int32_t beam;            /* PIC_BEAM_* */
+    int32_t envelope;        /* plane wave: PIC_ENV_SIN2 (sin^2 on [0, 2 FWHM]) or PIC_ENV_GAUSS (Sec. 3.1) */
+    int32_t remove_margin;   /* cells; <= 0: 3 */
+    double a0;               /* plane wave: field amplitude E0 = B0; LP/RP: peak of the on-axis focal
+                                field envelope (LP: E_x, RP: E_z) used to derive Psi_0 */
+    double duration;         /* field-amplitude FWHM (plane wave envelope; LP/RP on-axis focal envelope) */
+    double w0;               /* LP/RP waist: k^2 w0^2 = 2(sqrt(1+(ka)^2)-1) gives a (Sec. 4.1) */
+    double phi0;             /* constant phase (Eq. poisson) / plane-wave carrier phase */
+    double t_focus;          /* LP/RP: time the pulse crosses the focus; Gaussian plane wave: centre */
+    double focus[3];         /* LP/RP focus; plane wave: focus[0] is the plane where xi = t */
+    double a_param;          /* LP/RP overrides, used when > 0 (else derived): a, s, Psi_0 */
+    double s_param;
+    double psi0;
+    double e_unif[3];        /* PIC_BEAM_UNIFORM: constant external E and B */
+    double b_unif[3];
+    int32_t slab_lo[3];      /* electron slab, cells [lo, hi) per resolved axis */
+    int32_t slab_hi[3];
+    double n_e;              /* slab electron density (n_c) */
+    int32_t ppc;             /* particles per slab cell (0: no slab) */
+    int32_t tile[3];         /* particle tile in cells (x a multiple of 4); 0: chosen by the autotuner */
+    uint64_t seed;           /* SplitMix64 seed of the slab positions */
+    int64_t max_particles;   /* particle capacity; 0: slab count (pic_set_particles may need more) */
+    int64_t max_exits;       /* exit-record capacity; 0: max_particles */
+} pic_config;
+
+/* Host-side derived quantities (pic_derive_params, pic_info). */
+typedef struct {
+    double a, s, psi0;       /* LP/RP pulse parameters (0 for other beams) */
+    double dt;               /* time step actually used */
+    int64_t n_particles;     /* seeded slab particles */
+    int64_t device_bytes;    /* device memory pic_init will request */
+    int32_t tile[3];         /* particle tile after autotuning */
+    int32_t yee_tile[3];     /* field-solver tile */
+} pic_params;
+
+typedef struct {
+    int64_t step;            /* steps taken */
+    double time;             /* step * dt */
+    int64_t n_alive;         /* particles in the box */
+    int64_t n_exits;         /* exit records stored */
+    uint32_t status;         /* PIC_FLAG_* bits seen so far */
+    pic_params params;
+} pic_info;
+
+/* Device memory provider.  alloc(bytes, ctx) returns device memory (256-byte aligned)
+ * or NULL; free(ptr, ctx) releases it.  Both are called only from pic_init and
+ * pic_destroy on the calling thread.  A NULL pic_allocator* means cudaMalloc/cudaFree. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+} pic_allocator;
+
+typedef struct pic_sim pic_sim;
+
+/* ---- parameters (host only, no device needed) ------------------------------------ */
+/* Validates cfg and fills out: a from w0 (Sec. 4.1 waist relation), s from `duration`
+ * (field FWHM of the on-axis focal envelope), Psi_0 from a0 (peak of that envelope),
+ * dt, particle count, tiles and the device footprint.  Returns PIC_EINVAL with a
+ * message for an invalid configuration. */
+pic_status pic_derive_params(const pic_config* cfg, pic_params* out);
+
+/* ---- lifecycle ------------------------------------------------------------------- */
+/* Creates a simulation on the current CUDA device: allocates its device state through
+ * `alloc`, places the seeded slab (SplitMix64, particle p uses outputs 3p+d; offset =
+ * top 24 bits / 2^24), zeroes the scattered field and captures the step as a CUDA
+ * graph.  Synchronous on `stream`.  *out is NULL on failure. */
+pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* stream, pic_sim** out);
+
+/* Advances n_steps >= 0 steps (one step: push + current deposition, particle re-sort,
+ * field update).  Asynchronous on `stream` (graph replays). */
+pic_status pic_step(pic_sim* sim, int n_steps, void* stream);
+
+/* Advances n_steps steps like pic_step but launches the kernels one by one with CUDA
+ * events recorded on `stream` between the phases, and returns in HOST seconds[5] the
+ * summed device time of each phase: [0] push + deposit, [1] tile scan, [2] particle
+ * scatter, [3] field solve, [4] step end.  Synchronous.  Used to time kernels live. */
+pic_status pic_profile_step(pic_sim* sim, int n_steps, void* stream, double* seconds);
+
+/* Releases all device state; synchronises the simulation's work first.  NULL is a no-op. */
+pic_status pic_destroy(pic_sim* sim);
+
+/* Message of the last failing call on `sim` (or of the calling thread when sim is NULL).
+ * The string stays valid until the next call on the same sim / thread. */
+const char* pic_last_error(const pic_sim* sim);
+
+/* Step counter, particle counts and status word.  Synchronises `stream`. */
+pic_status pic_info_get(pic_sim* sim, pic_info* out, void* stream);
+
+/* ---- explicit state (inputs, checkpoint / restore) -------------------------------- */
+/* Replaces every particle.  HOST arrays: x[n][3] grid coordinates (unused axes ignored),
+ * u[n][3] momenta (gamma v), w[n] weights (density per particle, n_c), id[n] >= 0 and
+ * < 2^31.  Particles must lie inside the box, at least remove_margin cells from every
+ * face (else PIC_EINVAL).  n may exceed the slab count up to max_particles.
+ * Synchronous on `stream`. */
+pic_status pic_set_particles(pic_sim* sim, int64_t n, const double* x, const double* u,
+                             const double* w, const int64_t* id, void* stream);
+
+/* Replaces the grid fields.  HOST array of 9 components (Ex Ey Ez Bx By Bz Jx Jy Jz),
+ * each ext_z*ext_y*ext_x doubles, x fastest, ext = n+1 on resolved axes and 1 otherwise;
+ * points a component does not have (index n along a staggered axis) are ignored.
+ * The magnetic field is the one at the same integer time as E.  Synchronous. */
+pic_status pic_set_fields(pic_sim* sim, const double* fields, void* stream);
+
+/* Moves the step counter (time = step * dt); used with restored state.  Synchronous. */
+pic_status pic_set_step(pic_sim* sim, int64_t step, void* stream);
+
+/* ---- diagnostics (synchronous on `stream`; HOST output owned by the caller) -------- */
+enum {
+    PIC_DIAG_ENERGIES = 0,   /* double[8]: EM energy of the scattered field, EM energy of scattered +
+                                incident field on the grid points, kinetic energy sum w(gamma-1)dx^dim
+                                of the electrons in the box, kinetic energy carried out by exits,
+                                n_alive, n_exits, step, time */
+    PIC_DIAG_GAUSS = 1,      /* double[1]: max |div E - rho_e - rho_ion| over interior nodes, with
+                                rho_ion = -rho_e at step 0 (immobile ions) */
+    PIC_DIAG_PARTICLES = 2,  /* n_alive records of 8 doubles: x[3], u[3], w, id (as double) */
+    PIC_DIAG_EXITS = 3,      /* n_exits records of 6 doubles: u[3] at exit, w, id, step of exit */
+    PIC_DIAG_FIELDS = 4      /* double[9][ext_z][ext_y][ext_x] as in pic_set_fields (absent points 0) */
+};
+/* Writes diagnostic `kind` into host_out, which must hold at least the bytes the kind
+ * needs (PIC_ECAPACITY otherwise; pic_info_get gives the counts).  Returns PIC_ETIMEOUT
+ * if the device status word has the timeout bit, PIC_ENAN if an energy is not finite. */
+pic_status pic_diag(pic_sim* sim, int kind, void* host_out, size_t bytes, void* stream);
+
+/* Weighted electron histogram over kinetic energy gamma-1 in [0, e_max) (n_e bins) and
+ * angle from the +x (propagation) axis in [0, pi] (n_a bins); electrons in the box plus
+ * exits.  HOST output: double[n_e * n_a], angle fastest.  Synchronous. */
+pic_status pic_histogram(pic_sim* sim, int n_e, double e_max, int n_a, double* host_out, void* stream);
+
+/* Evaluates the simulation's incident field with the device code path at n HOST points
+ * pts[n][4] = (x, y, z, t) in grid coordinates; HOST out[n][6] = Ex Ey Ez Bx By Bz.
+ * Synchronous.  Used to check the incident-field arithmetic point by point. */
+pic_status pic_eval_incident(pic_sim* sim, int64_t n, const double* pts, double* out, void* stream);
+
+/* ---- batching: many independent simulations per launch --------------------------- */
+/* Advances every sim by n_steps: one persistent launch per phase over all their tiles
+ * (sims grouped by dim and precision), the whole step captured as one CUDA graph that is
+ * cached for this exact list.  All sims must live on the current device.  Asynchronous. */
+pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, void* stream);
+
+/* ---- serving: continuous batching of a request stream ----------------------------- */
+typedef struct pic_server pic_server;
+typedef struct {
+    int64_t memory_budget;   /* device bytes the resident simulations may use; 0: 80% of free memory */
+    int32_t max_resident;    /* simulations on the device at once; 0: 256 */
+    int32_t quantum;         /* steps advanced between admission rounds; 0: 50 */
+} pic_serve_config;
+typedef struct {
+    int32_t state;           /* 0 queued, 1 running, 2 done, -1 failed */
+    int32_t error;           /* pic_status of a failed request */
+    int64_t steps_done;
+    double submit_time;      /* seconds on the server clock */
+    double start_time;
+    double finish_time;
+    double energies[8];      /* PIC_DIAG_ENERGIES at completion */
+    int64_t pushes;          /* particle pushes performed */
+} pic_result;
+
+/* Starts a server with a host scheduling thread on the current device. */
+pic_status pic_serve_open(const pic_serve_config* cfg, pic_server** out);
+/* Queues a simulation request of n_steps; *ticket identifies it.  Thread safe. */
+pic_status pic_serve_submit(pic_server* srv, const pic_config* cfg, int64_t n_steps, uint64_t* ticket);
+/* Fills *out; returns PIC_EBUSY while the request is queued or running. Thread safe. */
+pic_status pic_serve_poll(pic_server* srv, uint64_t ticket, pic_result* out);
+/* Seconds on the server clock (the clock of pic_result times). */
+double pic_serve_clock(const pic_server* srv);
+/* Finishes running requests, stops the thread, frees everything. */
+pic_status pic_serve_close(pic_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFPIC_PIC_H */

@@ -796,6 +796,8 @@ void orc_step(orc_sim* s, int nsteps)
     for (int it = 0; it < nsteps; it++) {
         double t = s->step * dt;
         int64_t keep = 0;
+        /* J of this step; it stays readable after the step as J^{n+1/2} */
+        for (int c = 6; c < 9; c++) memset(s->F[c], 0, sizeof(double) * s->nnode);
         for (int64_t p = 0; p < s->np; p++) {
             double* x = &s->px[3 * p];
             double* u = &s->pu[3 * p];
@@ -852,7 +854,6 @@ void orc_step(orc_sim* s, int nsteps)
         }
         s->np = keep;
         yee(s);
-        for (int c = 6; c < 9; c++) memset(s->F[c], 0, sizeof(double) * s->nnode);
         s->step++;
     }
 }

@@ -67,7 +67,8 @@ void     orc_get_particles(const orc_sim* s, double* x, double* u, double* w, in
 void     orc_get_exits(const orc_sim* s, double* u, double* w, int64_t* id, int64_t* step);
 /* field arrays: 9 components (Ex Ey Ez Bx By Bz Jx Jy Jz), each ext[2]*ext[1]*ext[0]
  * doubles, x fastest, ext[d] = n[d]+1 on a resolved axis and 1 otherwise.
- * Index i along an axis on which the component is staggered means position i+1/2. */
+ * Index i along an axis on which the component is staggered means position i+1/2.
+ * After a step, J holds that step's J^{n+1/2}. */
 void     orc_extents(const orc_sim* s, int ext[3]);
 void     orc_get_fields(const orc_sim* s, double* out);
 void     orc_set_fields(orc_sim* s, const double* in);

@@ -1,0 +1,202 @@
+// Batched stepping of independent simulations (pic_batch_step): simulations of the
+// same dimension and precision form one launch group; each phase of the step (push +
+// deposit, tile scan, scatter, field solve, step end) is ONE persistent launch over the
+// (simulation, tile) work items of the whole group, pulled from a device counter.  The
+// step of all groups is captured once as a CUDA graph, cached per exact list of sims.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sim_internal.h"
+
+namespace {
+
+struct GroupRes {
+    Group g{};
+    void* mem = nullptr;
+};
+
+struct BatchEntry {
+    std::vector<pic_sim*> sims;
+    std::vector<GroupRes> groups;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+};
+
+std::mutex g_mu;
+std::map<std::vector<pic_sim*>, BatchEntry*> g_batches;
+
+void free_entry(BatchEntry* e)
+{
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->cs) cudaStreamDestroy(e->cs);
+    for (auto& gr : e->groups)
+        if (gr.mem) cudaFree(gr.mem);
+    delete e;
+}
+
+size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+
+pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std::string& err)
+{
+    std::map<std::pair<int, int>, std::vector<int>> by;
+    for (int i = 0; i < (int)sims.size(); ++i) by[{sims[i]->cfg.dim, sims[i]->cfg.precision}].push_back(i);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    BatchEntry* e = new BatchEntry();
+    e->sims = sims;
+    for (auto& kv : by) {
+        const std::vector<int>& mem = kv.second;
+        const int n = (int)mem.size();
+        long long npw = 0, nyw = 0;
+        size_t psm = 0, ysm = 0;
+        for (int i : mem) {
+            npw += sims[i]->h.nptiles;
+            nyw += sims[i]->h.nytiles;
+            psm = std::max(psm, sims[i]->grp.push_smem);
+            ysm = std::max(ysm, sims[i]->grp.yee_smem);
+        }
+        const size_t bytes = a256(sizeof(SimDev) * n) + a256(sizeof(Work) * npw) + a256(sizeof(Work) * nyw) +
+                             a256(sizeof(int) * n) + a256(64);
+        GroupRes gr;
+        if (cudaMalloc(&gr.mem, bytes) != cudaSuccess) {
+            err = "batch descriptor allocation failed";
+            free_entry(e);
+            return PIC_ENOMEM;
+        }
+        char* p = (char*)gr.mem;
+        SimDev* d_sims = (SimDev*)p;
+        p += a256(sizeof(SimDev) * n);
+        Work* d_pw = (Work*)p;
+        p += a256(sizeof(Work) * npw);
+        Work* d_yw = (Work*)p;
+        p += a256(sizeof(Work) * nyw);
+        int* d_list = (int*)p;
+        p += a256(sizeof(int) * n);
+        int* d_cnt = (int*)p;
+        std::vector<SimDev> hs(n);
+        std::vector<Work> pw, yw;
+        std::vector<int> list(n);
+        pw.reserve(npw);
+        yw.reserve(nyw);
+        for (int k = 0; k < n; ++k) {
+            pic_sim* s = sims[mem[k]];
+            hs[k] = s->h;
+            list[k] = k;
+            for (int t = 0; t < s->h.nptiles; ++t) pw.push_back({k, t});
+            for (int t = 0; t < s->h.nytiles; ++t) yw.push_back({k, t});
+        }
+        cudaMemcpy(d_sims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_pw, pw.data(), sizeof(Work) * npw, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_yw, yw.data(), sizeof(Work) * nyw, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_list, list.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+        cudaMemset(d_cnt, 0, 64);
+        Group& g = gr.g;
+        g.sims = d_sims;
+        g.pwork = d_pw;
+        g.npwork = (int)npw;
+        g.ywork = d_yw;
+        g.nywork = (int)nyw;
+        g.simlist = d_list;
+        g.nsims = n;
+        g.counters = d_cnt;
+        g.dim = kv.first.first;
+        g.prec = kv.first.second;
+        g.push_smem = psm;
+        g.yee_smem = ysm;
+        const int nsm = prop.multiProcessorCount;
+        const int bp = std::max(1, sff::prepare_push(g.dim, g.prec, psm));
+        const int byy = std::max(1, sff::prepare_yee(g.dim, g.prec, ysm));
+        const int bs = std::max(1, sff::scatter_blocks_per_sm(g.dim, g.prec));
+        g.push_grid = (int)std::max<long long>(1, std::min<long long>(npw, (long long)bp * nsm));
+        g.yee_grid = (int)std::max<long long>(1, std::min<long long>(nyw, (long long)byy * nsm));
+        g.scatter_grid = (int)std::max<long long>(1, std::min<long long>(npw, (long long)bs * nsm));
+        e->groups.push_back(gr);
+    }
+    if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamBeginCapture(e->cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        err = "batch capture could not start";
+        free_entry(e);
+        return PIC_ECUDA;
+    }
+    for (auto& gr : e->groups) {
+        sff::launch_push(gr.g, e->cs);
+        sff::launch_scan(gr.g, e->cs);
+        sff::launch_scatter(gr.g, e->cs);
+        sff::launch_yee(gr.g, e->cs);
+        sff::launch_step_end(gr.g, e->cs);
+    }
+    cudaError_t ce = cudaStreamEndCapture(e->cs, &e->graph);
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e->exec, e->graph, 0);
+    if (ce != cudaSuccess) {
+        err = std::string("batch graph: ") + cudaGetErrorString(ce);
+        free_entry(e);
+        return PIC_ECUDA;
+    }
+    *out = e;
+    return PIC_OK;
+}
+
+}  // namespace
+
+void batch_forget(pic_sim* s)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        if (std::find(it->first.begin(), it->first.end(), s) != it->first.end()) {
+            free_entry(it->second);
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+extern "C" pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, void* stream)
+{
+    if (!sims || n_sims <= 0 || n_steps < 0) return PIC_EINVAL;
+    std::vector<pic_sim*> key(sims, sims + n_sims);
+    for (pic_sim* s : key)
+        if (!s) return PIC_EINVAL;
+    {
+        std::vector<pic_sim*> u = key;
+        std::sort(u.begin(), u.end());
+        if (std::adjacent_find(u.begin(), u.end()) != u.end()) {
+            key[0]->err = "a simulation appears twice in the batch";
+            return PIC_EINVAL;
+        }
+    }
+    BatchEntry* e = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_batches.find(key);
+        if (it != g_batches.end()) {
+            e = it->second;
+        } else {
+            std::string err;
+            pic_status r = build_entry(key, &e, err);
+            if (r != PIC_OK) {
+                key[0]->err = err;
+                return r;
+            }
+            g_batches[key] = e;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n_steps; ++i) {
+        cudaError_t ce = cudaGraphLaunch(e->exec, st);
+        if (ce != cudaSuccess) {
+            key[0]->err = std::string("batch graph launch: ") + cudaGetErrorString(ce);
+            return PIC_ECUDA;
+        }
+    }
+    return PIC_OK;
+}

@@ -1,0 +1,736 @@
+// Particle kernels of the scattered-field PIC step (sm_103a):
+//   k_push     gather + incident field + Boris + move + Esirkepov deposit, one particle tile
+//              per work item: the tile's field box arrives by one TMA load, the current is
+//              accumulated in shared memory and leaves by one TMA reduce-add (FP32) or one
+//              atomic per nonzero cell (FP64); destination-tile counts are histogrammed in
+//              shared memory first (one global atomic per neighbour tile);
+//   k_scan     per-simulation exclusive scan of the destination-tile counts;
+//   k_scatter  stable-by-tile compaction into the other buffer set with warp-aggregated
+//              slot reservation;
+//   k_step_end step counter and buffer parity.
+// Set-up kernels generate the seeded slab and sort arbitrary particle sets by tile.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "beam.cuh"
+#include "sff_common.cuh"
+#include "sff_kernels.h"
+
+namespace sff {
+
+template <typename R>
+__device__ __forceinline__ void shape2(R d, R w[3])
+{
+    const R a = R(0.5) - d, b = R(0.5) + d;
+    w[0] = R(0.5) * a * a;
+    w[1] = R(0.75) - d * d;
+    w[2] = R(0.5) * b * b;
+}
+
+template <int D>
+__device__ __forceinline__ void decode_cell(const SimDev& S, unsigned cl, int c[3])
+{
+    c[0] = (int)(cl & ((1u << S.cb[0]) - 1u));
+    c[1] = 0;
+    c[2] = 0;
+    if constexpr (D > 1) c[1] = (int)((cl >> S.cb[0]) & ((1u << S.cb[1]) - 1u));
+    if constexpr (D > 2) c[2] = (int)(cl >> (S.cb[0] + S.cb[1]));
+}
+
+template <int D>
+__device__ __forceinline__ unsigned encode_cell(const SimDev& S, const int c[3])
+{
+    unsigned v = (unsigned)c[0];
+    if constexpr (D > 1) v |= (unsigned)c[1] << S.cb[0];
+    if constexpr (D > 2) v |= (unsigned)c[2] << (S.cb[0] + S.cb[1]);
+    return v;
+}
+
+template <int D>
+__device__ __forceinline__ int tile_of(const SimDev& S, const int c[3])
+{
+    int t = c[0] / S.pt[0];
+    if constexpr (D > 1) t += S.npt[0] * (c[1] / S.pt[1]);
+    if constexpr (D > 2) t += S.npt[0] * S.npt[1] * (c[2] / S.pt[2]);
+    return t;
+}
+
+// order-2 interpolation from a shared-memory box [bz][by][bx]
+template <int D, typename R>
+__device__ __forceinline__ R interp(const R* f, int bx, int bxy, const int b0, const int b1, const int b2,
+                                    const R* w0, const R* w1, const R* w2)
+{
+    if constexpr (D == 1) {
+        return w0[0] * f[b0] + w0[1] * f[b0 + 1] + w0[2] * f[b0 + 2];
+    } else if constexpr (D == 2) {
+        R v = R(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const R* r = f + (b1 + j) * bx + b0;
+            v += w1[j] * (w0[0] * r[0] + w0[1] * r[1] + w0[2] * r[2]);
+        }
+        return v;
+    } else {
+        R v = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R vk = R(0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const R* r = f + (b2 + k) * bxy + (b1 + j) * bx + b0;
+                vk += w1[j] * (w0[0] * r[0] + w0[1] * r[1] + w0[2] * r[2]);
+            }
+            v += w2[k] * vk;
+        }
+        return v;
+    }
+}
+
+__device__ __forceinline__ void sm_add(float* a, float v)
+{
+    if (v != 0.0f) atomicAdd(a, v);
+}
+__device__ __forceinline__ void sm_add(double* a, double v)
+{
+    if (v != 0.0) atomicAdd(a, v);
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_push(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+                                              int nwork, int* __restrict__ counter)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item;
+    __shared__ int s_hist[27];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nwork) break;
+        const Work wk = work[item];
+        const SimDev& S = sims[wk.sim];
+        DevState* st = S.st;
+        const int par = st->parity;
+        const int p0 = S.toff[par][wk.tile], p1 = S.toff[par][wk.tile + 1];
+        if (p0 >= p1) continue;
+
+        int tc[3] = {0, 0, 0};
+        {
+            int t = wk.tile;
+            tc[0] = t % S.npt[0];
+            t /= S.npt[0];
+            if constexpr (D > 1) {
+                tc[1] = t % S.npt[1];
+                t /= S.npt[1];
+            }
+            if constexpr (D > 2) tc[2] = t;
+        }
+        const int T0[3] = {tc[0] * S.pt[0], tc[1] * S.pt[1], tc[2] * S.pt[2]};
+        const int bx = S.pb[0], by = D > 1 ? S.pb[1] : 1, bz = D > 2 ? S.pb[2] : 1;
+        const int bxy = bx * by, bvol = bxy * bz;
+        R* Fs = reinterpret_cast<R*>(smem_raw);   // [6][bz][by][bx]: Ex Ey Ez Bx By Bz at step n
+        R* Js = reinterpret_cast<R*>(smem_raw + round128(6 * bvol * sizeof(R)));   // [3][bz][by][bx]
+        // box: x nodes [T0-4, T0+pt+4), y/z nodes [T0-2, T0+pt+3); array index = node + G
+        const int org[3] = {T0[0] - 4 + G, D > 1 ? T0[1] - 2 + G : 0, D > 2 ? T0[2] - 2 + G : 0};
+        if (tid == 0) {
+            tensormap_acquire(&S.tm_pf);
+            tensormap_acquire(&S.tm_pj);
+            mbar_arrive_expect_tx(&bar, (unsigned)(6 * bvol * sizeof(R)));
+            tma_load_box<D>(Fs, &S.tm_pf, org, comp_eb(par), &bar);
+        }
+        for (int i = tid; i < 3 * bvol; i += nth) Js[i] = R(0);
+        if (tid < 27) s_hist[tid] = 0;
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&st->status, (unsigned)FLAG_TIMEOUT);
+                mbar_wait_bounded(&bar, phase ^ 1u);
+                bulk_wait0();
+            }
+            return;
+        }
+
+        const BeamC<R> bc = beam_consts<R>(S);
+        const double t = (double)st->step * S.dt;
+        const R dt = R(S.dt);
+        const R dtdx = R(S.dt * S.inv_dx);
+        const R jfac = R(S.dx / S.dt);              // -q dx/dt, q = -1
+        const R hq = R(-0.5 * S.dt);                // q dt / 2
+        const int hx[3] = {4, 2, 2};                // box halo below the tile per axis
+
+        for (int p = p0 + tid; p < p1; p += nth) {
+            const unsigned cl = S.cell[par][p];
+            int c[3];
+            decode_cell<D>(S, cl, c);
+            R o[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int d = 0; d < D; ++d) o[d] = reinterpret_cast<const R*>(S.off[par][d])[p];
+            R u[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) u[d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
+            const R wt = reinterpret_cast<const R*>(S.wgt[par])[p];
+
+            // ---- gather of the scattered field (order-2 shapes on the Yee stagger) ----
+            R Wp[3][3], Wd[3][3];
+            int lp[3] = {0, 0, 0}, ld[3] = {0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < D) {
+                    const int h = o[d] >= R(0.5);
+                    shape2(o[d] - R(h), Wp[d]);
+                    lp[d] = c[d] + h - 1 - T0[d] + hx[d];
+                    shape2(o[d] - R(0.5), Wd[d]);
+                    ld[d] = c[d] - 1 - T0[d] + hx[d];
+                } else {
+                    Wp[d][0] = Wd[d][0] = R(1);
+                    Wp[d][1] = Wd[d][1] = Wp[d][2] = Wd[d][2] = R(0);
+                }
+            }
+            R E[3], B[3];
+            E[0] = interp<D, R>(Fs + 0 * bvol, bx, bxy, ld[0], lp[1], lp[2], Wd[0], Wp[1], Wp[2]);
+            E[1] = interp<D, R>(Fs + 1 * bvol, bx, bxy, lp[0], ld[1], lp[2], Wp[0], Wd[1], Wp[2]);
+            E[2] = interp<D, R>(Fs + 2 * bvol, bx, bxy, lp[0], lp[1], ld[2], Wp[0], Wp[1], Wd[2]);
+            B[0] = interp<D, R>(Fs + 3 * bvol, bx, bxy, lp[0], ld[1], ld[2], Wp[0], Wd[1], Wd[2]);
+            B[1] = interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
+            B[2] = interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
+
+            // ---- incident field at (x^n, t^n) ----
+            {
+                R Ei[3], Bi[3];
+                incident_at<D, R>(S, bc, c, o, t, Ei, Bi);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    E[d] += Ei[d];
+                    B[d] += Bi[d];
+                }
+            }
+
+            // ---- relativistic Boris push, charge -1, mass 1 ----
+            R um[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) um[d] = u[d] + hq * E[d];
+            const R gm = m_sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+            const R tf = hq / gm;
+            const R tv[3] = {tf * B[0], tf * B[1], tf * B[2]};
+            const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+            const R sf = R(2) / (R(1) + t2);
+            const R up[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]), um[1] + (um[2] * tv[0] - um[0] * tv[2]),
+                             um[2] + (um[0] * tv[1] - um[1] * tv[0])};
+            const R sv[3] = {sf * tv[0], sf * tv[1], sf * tv[2]};
+            u[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + hq * E[0];
+            u[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + hq * E[1];
+            u[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + hq * E[2];
+            const R ig = R(1) / m_sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            const R v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
+
+            // ---- Esirkepov deposition of the move (shapes relative to the old nearest node) ----
+            R S0[3][5], DS[3][5];
+            int jb[3] = {0, 0, 0};
+            R mv[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                mv[d] = dtdx * v[d];
+                const int h0 = o[d] >= R(0.5);
+                const R d0 = o[d] - R(h0);
+                const R r1 = d0 + mv[d];
+                const int sh = (int)m_floor(r1 + R(0.5));
+                const R d1 = r1 - R(sh);
+                R w0[3], w1[3];
+                shape2(d0, w0);
+                shape2(d1, w1);
+                R s1[5] = {R(0), R(0), R(0), R(0), R(0)};
+                if (sh < 0) {
+                    s1[0] = w1[0]; s1[1] = w1[1]; s1[2] = w1[2];
+                } else if (sh == 0) {
+                    s1[1] = w1[0]; s1[2] = w1[1]; s1[3] = w1[2];
+                } else {
+                    s1[2] = w1[0]; s1[3] = w1[1]; s1[4] = w1[2];
+                }
+                S0[d][0] = R(0); S0[d][1] = w0[0]; S0[d][2] = w0[1]; S0[d][3] = w0[2]; S0[d][4] = R(0);
+#pragma unroll
+                for (int m = 0; m < 5; ++m) DS[d][m] = s1[m] - S0[d][m];
+                jb[d] = c[d] + h0 - 2 - T0[d] + hx[d];
+            }
+            R* Jx = Js;
+            R* Jy = Js + bvol;
+            R* Jz = Js + 2 * bvol;
+            const R cw = jfac * wt;
+            const R third = R(1) / R(3);
+            if constexpr (D == 1) {
+                R acc = R(0);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc += cw * DS[0][a];
+                    sm_add(&Jx[jb[0] + a], acc);
+                }
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    const R f = S0[0][a] + R(0.5) * DS[0][a];
+                    sm_add(&Jy[jb[0] + a], -wt * v[1] * f);
+                    sm_add(&Jz[jb[0] + a], -wt * v[2] * f);
+                }
+            } else if constexpr (D == 2) {
+#pragma unroll
+                for (int b = 0; b < 5; ++b) {
+                    const R fy = S0[1][b] + R(0.5) * DS[1][b];
+                    R acc = R(0);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        acc += cw * DS[0][a] * fy;
+                        sm_add(&Jx[(jb[1] + b) * bx + jb[0] + a], acc);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    const R fx = S0[0][a] + R(0.5) * DS[0][a];
+                    R acc = R(0);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        acc += cw * DS[1][b] * fx;
+                        sm_add(&Jy[(jb[1] + b) * bx + jb[0] + a], acc);
+                    }
+                }
+                const R qv = -wt * v[2];
+#pragma unroll
+                for (int b = 0; b < 5; ++b)
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        const R wz = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
+                                     R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
+                        sm_add(&Jz[(jb[1] + b) * bx + jb[0] + a], qv * wz);
+                    }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < 5; ++cc)
+#pragma unroll
+                    for (int b = 0; b < 5; ++b) {
+                        const R fyz = S0[1][b] * S0[2][cc] + R(0.5) * DS[1][b] * S0[2][cc] +
+                                      R(0.5) * S0[1][b] * DS[2][cc] + third * DS[1][b] * DS[2][cc];
+                        R acc = R(0);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            acc += cw * DS[0][a] * fyz;
+                            sm_add(&Jx[(jb[2] + cc) * bxy + (jb[1] + b) * bx + jb[0] + a], acc);
+                        }
+                    }
+#pragma unroll
+                for (int cc = 0; cc < 5; ++cc)
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        const R fxz = S0[0][a] * S0[2][cc] + R(0.5) * DS[0][a] * S0[2][cc] +
+                                      R(0.5) * S0[0][a] * DS[2][cc] + third * DS[0][a] * DS[2][cc];
+                        R acc = R(0);
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            acc += cw * DS[1][b] * fxz;
+                            sm_add(&Jy[(jb[2] + cc) * bxy + (jb[1] + b) * bx + jb[0] + a], acc);
+                        }
+                    }
+#pragma unroll
+                for (int b = 0; b < 5; ++b)
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        const R fxy = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
+                                      R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
+                        R acc = R(0);
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) {
+                            acc += cw * DS[2][cc] * fxy;
+                            sm_add(&Jz[(jb[2] + cc) * bxy + (jb[1] + b) * bx + jb[0] + a], acc);
+                        }
+                    }
+            }
+
+            // ---- move: carry the offset into the cell index; removal near the faces ----
+            int cn[3] = {c[0], c[1], c[2]};
+            R on[3] = {R(0), R(0), R(0)};
+            bool dead = false;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const R x = o[d] + mv[d];
+                const R fl = m_floor(x);
+                R r = x - fl;
+                int k = (int)fl;
+                if (r >= R(1)) {
+                    r -= R(1);
+                    k += 1;
+                }
+                cn[d] = c[d] + k;
+                on[d] = r;
+                if (cn[d] < S.margin || cn[d] >= S.n[d] - S.margin) dead = true;
+            }
+            unsigned ncl = DEAD;
+            if (dead) {
+                const int slot = atomicAdd(&st->n_exits, 1);
+                if (slot < S.max_exits) {
+                    double* e = S.exits + (long long)slot * EXIT_DOUBLES;
+                    e[0] = (double)u[0];
+                    e[1] = (double)u[1];
+                    e[2] = (double)u[2];
+                    e[3] = (double)wt;
+                    e[4] = (double)S.pid[par][p];
+                    e[5] = (double)st->step;
+                } else {
+                    atomicOr(&st->status, (unsigned)FLAG_EXIT_OVERFLOW);
+                }
+            } else {
+                int hidx = 0, mul = 1;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    hidx += (cn[d] / S.pt[d] - tc[d] + 1) * mul;
+                    mul *= 3;
+                }
+                atomicAdd(&s_hist[hidx], 1);
+                ncl = encode_cell<D>(S, cn);
+            }
+            S.cell[par][p] = ncl;
+#pragma unroll
+            for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
+        }
+        __syncthreads();
+
+        // ---- current flush and destination-tile counts ----
+        if constexpr (sizeof(R) == 4) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_reduce_add_box<D>(&S.tm_pj, org, comp_j(par), Js);
+                bulk_commit();
+            }
+        } else {
+            R* Fg = reinterpret_cast<R*>(S.F);
+            const long long jbase = (long long)comp_j(par) * S.sc;
+            for (int i = tid; i < 3 * bvol; i += nth) {
+                const R val = Js[i];
+                if (val != R(0)) {
+                    const int comp = i / bvol, rem = i - comp * bvol;
+                    const int lz = rem / bxy, rxy = rem - lz * bxy, ly = rxy / bx, lx = rxy - ly * bx;
+                    atomicAdd(&Fg[jbase + comp * S.sc + (long long)(org[2] + lz) * S.sz +
+                                  (long long)(org[1] + ly) * S.sy + (org[0] + lx)],
+                              val);
+                }
+            }
+        }
+        constexpr int NH = D == 1 ? 3 : (D == 2 ? 9 : 27);
+        if (tid < NH && s_hist[tid] > 0) {
+            int h = tid, nt = 0, mul = 1;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                nt += (tc[d] + (h % 3) - 1) * mul;
+                h /= 3;
+                mul *= S.npt[d];
+            }
+            atomicAdd(&S.tcnt[nt], s_hist[tid]);
+        }
+        if constexpr (sizeof(R) == 4) {
+            if (tid == 0) bulk_wait_read0();
+        }
+        __syncthreads();
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+// Exclusive scan of the destination counts of one simulation per block (1024 threads).
+__device__ void scan_counts(const SimDev& S, int outpar)
+{
+    __shared__ int s_warp[32];
+    const int n = S.nptiles;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int chunk = (n + nth - 1) / nth;
+    const int i0 = min(n, tid * chunk), i1 = min(n, i0 + chunk);
+    int local = 0;
+    for (int i = i0; i < i1; ++i) local += S.tcnt[i];
+    // block exclusive scan of `local`
+    const int lane = tid & 31, wid = tid >> 5;
+    int x = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (nth >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int run = x - local + (wid > 0 ? s_warp[wid - 1] : 0);
+    int* out = S.toff[outpar];
+    for (int i = i0; i < i1; ++i) {
+        out[i] = run;
+        run += S.tcnt[i];
+        S.tcnt[i] = 0;
+        S.tcur[i] = 0;
+    }
+    if (tid == nth - 1) out[n] = run;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims, const int* __restrict__ list)
+{
+    const SimDev& S = sims[list[blockIdx.x]];
+    scan_counts(S, 1 - S.st->parity);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_one(const SimDev* __restrict__ sim)
+{
+    scan_counts(*sim, 1 - sim->st->parity);
+}
+
+template <int D, typename R>
+__device__ __forceinline__ void copy_particle(const SimDev& S, int from, long long p, int to, long long q)
+{
+    S.cell[to][q] = S.cell[from][p];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        reinterpret_cast<R*>(S.off[to][d])[q] = reinterpret_cast<const R*>(S.off[from][d])[p];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        reinterpret_cast<R*>(S.mom[to][d])[q] = reinterpret_cast<const R*>(S.mom[from][d])[p];
+    reinterpret_cast<R*>(S.wgt[to])[q] = reinterpret_cast<const R*>(S.wgt[from])[p];
+    S.pid[to][q] = S.pid[from][p];
+}
+
+// Reserve destination slots for a warp's particles (tile < 0: nothing to place).
+__device__ __forceinline__ int warp_reserve(int tile, int* cursors)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, tile);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (tile >= 0 && lane == leader) base = atomicAdd(&cursors[tile], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + rank;
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+                                                 int nwork, int* __restrict__ counter)
+{
+    __shared__ int s_item;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nwork) break;
+        const Work wk = work[item];
+        const SimDev& S = sims[wk.sim];
+        const int par = S.st->parity, np = 1 - par;
+        const int p0 = S.toff[par][wk.tile], p1 = S.toff[par][wk.tile + 1];
+        for (int base = p0; base < p1; base += nth) {
+            const int p = base + tid;
+            int t = -1;
+            if (p < p1) {
+                const unsigned cl = S.cell[par][p];
+                if (cl != DEAD) {
+                    int c[3];
+                    decode_cell<D>(S, cl, c);
+                    t = tile_of<D>(S, c);
+                }
+            }
+            const int slot = warp_reserve(t, S.tcur);
+            if (t >= 0) copy_particle<D, R>(S, par, p, np, (long long)S.toff[np][t] + slot);
+        }
+    }
+}
+
+__global__ void k_step_end(const SimDev* __restrict__ sims, const int* __restrict__ list, int nsims,
+                           int* __restrict__ counters)
+{
+    for (int i = threadIdx.x; i < nsims; i += blockDim.x) {
+        const SimDev& S = sims[list[i]];
+        DevState* st = S.st;
+        const int np = 1 - st->parity;
+        st->n_alive = S.toff[np][S.nptiles];
+        st->parity = np;
+        st->step += 1;
+    }
+    if (threadIdx.x < 4) counters[threadIdx.x] = 0;
+}
+
+// ---- set-up ----------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long k)
+{
+    // SplitMix64 (Steele, Lea & Flood 2014): k-th output of the stream seeded with `seed`
+    unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Seeded slab into buffer set 1, linear order; counts per tile.
+template <int D, typename R>
+__global__ void k_gen_slab(const SimDev* __restrict__ sim, long long n, int ppc, int lo0, int lo1, int lo2, int n0,
+                           int n1, unsigned long long seed, double weight)
+{
+    const SimDev& S = *sim;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long cellp = p / ppc;
+        const int lo[3] = {lo0, lo1, lo2};
+        const long long rel[3] = {cellp % n0, (cellp / n0) % n1, cellp / ((long long)n0 * n1)};
+        int c[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            c[d] = lo[d] + (int)rel[d];
+            const unsigned long long r = splitmix64(seed, 3ull * (unsigned long long)p + d);
+            const double offd = (double)(r >> 40) * (1.0 / 16777216.0);
+            reinterpret_cast<R*>(S.off[1][d])[p] = R(offd);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[1][d])[p] = R(0);
+        reinterpret_cast<R*>(S.wgt[1])[p] = R(weight);
+        S.pid[1][p] = (unsigned)p;
+        S.cell[1][p] = encode_cell<D>(S, c);
+        atomicAdd(&S.tcnt[tile_of<D>(S, c)], 1);
+    }
+}
+
+template <int D>
+__global__ void k_count_linear(const SimDev* __restrict__ sim, long long n)
+{
+    const SimDev& S = *sim;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        decode_cell<D>(S, S.cell[1][p], c);
+        atomicAdd(&S.tcnt[tile_of<D>(S, c)], 1);
+    }
+}
+
+// Set 1 (linear) -> set 0 (sorted by tile); toff[0] already scanned.
+template <int D, typename R>
+__global__ void k_sort_linear(const SimDev* __restrict__ sim, long long n)
+{
+    const SimDev& S = *sim;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nround = (n + stride - 1) / stride * stride;   // uniform trip count per warp
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nround; p += stride) {
+        int t = -1;
+        if (p < n) {
+            int c[3];
+            decode_cell<D>(S, S.cell[1][p], c);
+            t = tile_of<D>(S, c);
+        }
+        const int slot = warp_reserve(t, S.tcur);
+        if (t >= 0) copy_particle<D, R>(S, 1, p, 0, (long long)S.toff[0][t] + slot);
+    }
+}
+
+// ---- host launch wrappers ------------------------------------------------------------
+template <int D, typename R>
+static void push_t(const Group& g, cudaStream_t s)
+{
+    k_push<D, R><<<g.push_grid, 256, g.push_smem, s>>>(g.sims, g.pwork, g.npwork, g.counters + 0);
+}
+template <int D, typename R>
+static void scatter_t(const Group& g, cudaStream_t s)
+{
+    k_scatter<D, R><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.pwork, g.npwork, g.counters + 1);
+}
+
+#define SFF_DISPATCH(dim, prec, FN, ...)                                 \
+    do {                                                                 \
+        if ((prec) == 0) {                                               \
+            if ((dim) == 1) FN<1, double>(__VA_ARGS__);                  \
+            else if ((dim) == 2) FN<2, double>(__VA_ARGS__);             \
+            else FN<3, double>(__VA_ARGS__);                             \
+        } else {                                                         \
+            if ((dim) == 1) FN<1, float>(__VA_ARGS__);                   \
+            else if ((dim) == 2) FN<2, float>(__VA_ARGS__);              \
+            else FN<3, float>(__VA_ARGS__);                              \
+        }                                                                \
+    } while (0)
+
+void launch_push(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, push_t, g, s); }
+void launch_scatter(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, scatter_t, g, s); }
+void launch_scan(const Group& g, cudaStream_t s) { k_scan<<<g.nsims, 1024, 0, s>>>(g.sims, g.simlist); }
+void launch_step_end(const Group& g, cudaStream_t s)
+{
+    k_step_end<<<1, 256, 0, s>>>(g.sims, g.simlist, g.nsims, g.counters);
+}
+void launch_scan_one(const SimDev* sim, int, int, cudaStream_t s) { k_scan_one<<<1, 1024, 0, s>>>(sim); }
+
+template <int D, typename R>
+static void gen_t(const SimDev* sim, long long n, int ppc, const int lo[3], const int sn[3], unsigned long long seed,
+                  double w, cudaStream_t s)
+{
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (n > 0) k_gen_slab<D, R><<<grid, 256, 0, s>>>(sim, n, ppc, lo[0], lo[1], lo[2], sn[0], sn[1], seed, w);
+}
+void launch_gen_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int slab_lo[3],
+                     const int slab_n[3], unsigned long long seed, double weight, cudaStream_t s)
+{
+    SFF_DISPATCH(dim, prec, gen_t, sim, n, ppc, slab_lo, slab_n, seed, weight, s);
+}
+
+template <int D, typename R>
+static void count_t(const SimDev* sim, long long n, cudaStream_t s)
+{
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (n > 0) k_count_linear<D><<<grid, 256, 0, s>>>(sim, n);
+}
+void launch_count_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s)
+{
+    SFF_DISPATCH(dim, prec, count_t, sim, n, s);
+}
+
+template <int D, typename R>
+static void sortlin_t(const SimDev* sim, long long n, cudaStream_t s)
+{
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (n > 0) k_sort_linear<D, R><<<grid, 256, 0, s>>>(sim, n);
+}
+void launch_sort_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s)
+{
+    SFF_DISPATCH(dim, prec, sortlin_t, sim, n, s);
+}
+
+template <int D, typename R>
+static void attr_push(size_t smem, int* out)
+{
+    cudaFuncSetAttribute(k_push<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_push<D, R>, 256, smem);
+}
+int prepare_push(int dim, int prec, size_t smem)
+{
+    int b = 0;
+    SFF_DISPATCH(dim, prec, attr_push, smem, &b);
+    return b;
+}
+
+template <int D, typename R>
+static void attr_scatter(int* out)
+{
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_scatter<D, R>, 256, 0);
+}
+int scatter_blocks_per_sm(int dim, int prec)
+{
+    int b = 0;
+    SFF_DISPATCH(dim, prec, attr_scatter, &b);
+    return b;
+}
+
+}  // namespace sff

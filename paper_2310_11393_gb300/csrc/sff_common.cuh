@@ -1,0 +1,313 @@
+// Internal definitions shared by the kernels and the C-ABI of the GB300 (sm_103a)
+// scattered-field PIC library: per-simulation device descriptor, grid layout,
+// inline-PTX wrappers for mbarrier / TMA (cp.async.bulk.tensor) and a small
+// complex type.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sff {
+
+// Ghost points stored below (and at least this many above) every resolved axis.
+// Four keeps every TMA box start on the x axis a multiple of four elements.
+constexpr int G = 4;
+constexpr int NCOMP = 9;           // Ex Ey Ez Bx By Bz Jx Jy Jz
+constexpr unsigned DEAD = 0xFFFFFFFFu;
+constexpr int EXIT_DOUBLES = 6;    // u[3], w, id, step
+
+enum Beam { BEAM_NONE = 0, BEAM_PLANE = 1, BEAM_LP = 2, BEAM_RP = 3, BEAM_UNIFORM = 4 };
+enum Flag { FLAG_TIMEOUT = 1u, FLAG_CFL = 2u, FLAG_EXIT_OVERFLOW = 4u };
+
+// Device-updated state of one simulation.
+struct DevState {
+    long long step;       // steps taken; time = step * dt
+    int parity;           // which particle buffer set is current
+    int n_alive;
+    int n_exits;          // exit records claimed (may exceed capacity; then FLAG_EXIT_OVERFLOW)
+    unsigned status;
+    long long pad[5];
+};
+
+// Everything a kernel needs to know about one simulation.  Lives in device memory
+// (an array of these serves a batch); tensor maps must stay 64-byte aligned.
+struct alignas(128) SimDev {
+    CUtensorMap tm_pf;        // push box, field comps 0..5 (load)
+    CUtensorMap tm_pj;        // push box, current comps 6..8 (reduce-add, FP32)
+    CUtensorMap tm_yin;       // field-solver box, E and B comps (load)
+    CUtensorMap tm_yj;        // field-solver box, J comps (load)
+    CUtensorMap tm_yout;      // field-solver tile, E and B comps (store)
+
+    int dim, prec, beam, envelope;
+    int n[3];                 // cells per axis (1 on unresolved axes)
+    int na[3];                // allocated points per axis (1 on unresolved axes)
+    long long sy, sz, sc;     // element strides of y, z and component
+    int pt[3], npt[3];        // particle tile (cells) and tiles per axis
+    int nptiles;
+    int pb[3];                // particle box extent per axis
+    int yt[3], nyt[3];        // field-solver tile and tiles per axis
+    int nytiles;
+    int yb[3];                // field-solver box extent per axis
+    int cb[3];                // bits of each cell coordinate in the packed cell index
+    int margin;
+    int pad0;
+    double dx, dt, inv_dx;
+    // incident field
+    double a0, duration, phi0, t_focus, a, s, psi0;
+    double focus[3];
+    double e_unif[3], b_unif[3];
+    int icf[3];               // focus = (icf + frf) * dx per axis
+    float frf[3];
+    // device buffers
+    void* F;                  // fields: [9][na_z][na_y][na_x], element (0,0,0) is a ghost corner
+    unsigned* cell[2];        // packed cell index per particle (DEAD = removed)
+    void* off[2][3];          // in-cell offset in [0,1) per resolved axis
+    void* mom[2][3];          // momentum gamma*v
+    void* wgt[2];
+    unsigned* pid[2];
+    int* toff[2];             // tile offsets [nptiles + 1] of each buffer set
+    int* tcnt;                // per-tile counts of the next step
+    int* tcur;                // per-tile write cursors
+    double* exits;            // [max_exits][EXIT_DOUBLES]
+    long long max_exits;
+    long long cap;            // particle capacity per buffer set
+    DevState* st;
+    double* rho_ion;          // [na_z][na_y][na_x] ion charge density (diagnostics)
+    double* scratch;          // diagnostics scratch: charge density, same layout
+};
+
+struct Work {
+    int sim;
+    int tile;
+};
+
+// ---------------------------------------------------------------------------------
+// inline PTX: shared-memory addresses, mbarrier, TMA
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// smem sub-buffers used by TMA start on 128-byte boundaries
+__host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~size_t(127); }
+
+// acquire a tensor map that was written to global memory before the launch
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2^31 SM clocks (about one
+// second at 2 GHz) or 2^22 polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    long long t0 = clock64();
+    for (int i = 0; i < (1 << 22); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > (1ll << 31)) break;
+    }
+    return false;
+}
+
+// TMA tiled loads into shared memory, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// TMA element-wise add of a shared-memory box into global memory (performed at L2).
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* tm, int c0, int c1, const void* src)
+{
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c0), "r"(c1), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap* tm, int c0, int c1, int c2, const void* src)
+{
+    asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_4d(const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                                  const void* src)
+{
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.4d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+            reinterpret_cast<uint64_t>(tm)),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+        : "memory");
+}
+
+// TMA tiled stores from shared memory.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, int c0, int c1, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c0), "r"(c1), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int c1, int c2, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* tm, int c0, int c1, int c2, int c3, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Box load / reduce / store dispatch on the tensor rank (dim + 1: x, [y, [z,]] component).
+template <int D>
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* tm, const int c[3], int comp, uint64_t* bar)
+{
+    if constexpr (D == 1) tma_load_2d(dst, tm, c[0], comp, bar);
+    else if constexpr (D == 2) tma_load_3d(dst, tm, c[0], c[1], comp, bar);
+    else tma_load_4d(dst, tm, c[0], c[1], c[2], comp, bar);
+}
+template <int D>
+__device__ __forceinline__ void tma_reduce_add_box(const CUtensorMap* tm, const int c[3], int comp, const void* src)
+{
+    if constexpr (D == 1) tma_reduce_add_2d(tm, c[0], comp, src);
+    else if constexpr (D == 2) tma_reduce_add_3d(tm, c[0], c[1], comp, src);
+    else tma_reduce_add_4d(tm, c[0], c[1], c[2], comp, src);
+}
+template <int D>
+__device__ __forceinline__ void tma_store_box(const CUtensorMap* tm, const int c[3], int comp, const void* src)
+{
+    if constexpr (D == 1) tma_store_2d(tm, c[0], comp, src);
+    else if constexpr (D == 2) tma_store_3d(tm, c[0], c[1], comp, src);
+    else tma_store_4d(tm, c[0], c[1], c[2], comp, src);
+}
+
+// ---------------------------------------------------------------------------------
+// complex arithmetic in precision R
+// ---------------------------------------------------------------------------------
+template <typename R>
+struct Cx {
+    R x, y;
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator-(Cx<R> a) { return {-a.x, -a.y}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) { return {s * a.x, s * a.y}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> cinv(Cx<R> b)
+{
+    R d = R(1) / (b.x * b.x + b.y * b.y);
+    return {b.x * d, -b.y * d};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> operator/(Cx<R> a, Cx<R> b) { return a * cinv(b); }
+
+// math overloads (call CUDA's own functions)
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_hypot(float x, float y) { return hypotf(x, y); }
+__device__ __forceinline__ double m_hypot(double x, double y) { return hypot(x, y); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double m_exp2(double x) { return exp2(x); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ void m_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float m_sin(float x) { return sinf(x); }
+__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+__device__ __forceinline__ float m_sinpi(float x) { return sinpif(x); }
+__device__ __forceinline__ double m_sinpi(double x) { return sinpi(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+__device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double m_abs(double x) { return fabs(x); }
+
+template <typename R>
+__device__ __forceinline__ Cx<R> csqrt_(Cx<R> z)
+{
+    R m = m_hypot(z.x, z.y);
+    if (z.x >= R(0)) {
+        R t = m_sqrt((m + z.x) * R(0.5));
+        return {t, t > R(0) ? z.y / (R(2) * t) : R(0)};
+    }
+    R t = m_sqrt((m - z.x) * R(0.5));
+    return {m_abs(z.y) / (R(2) * t), z.y < R(0) ? -t : t};
+}
+
+}  // namespace sff

@@ -1,0 +1,65 @@
+// Host-side launch interface of the kernels (no CUDA types beyond the runtime's).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sff_common.cuh"
+
+namespace sff {
+
+// Field array layout: 18 components of na_z*na_y*na_x elements each:
+//   [0..5]  E, B of buffer set 0   [6..11] E, B of buffer set 1
+//   [12..14] J of set 0            [15..17] J of set 1
+// The push reads set p and deposits J_p; the field solver reads set p and J_p, writes
+// set 1-p and clears J_{1-p}.  p = DevState::parity flips at the end of each step.
+constexpr int NFCOMP = 18;
+__host__ __device__ constexpr int comp_eb(int parity) { return 6 * parity; }
+__host__ __device__ constexpr int comp_j(int parity) { return 12 + 3 * parity; }
+
+// One launch group: simulations of one dimension and precision advanced together.
+struct Group {
+    const SimDev* sims;    // device array
+    const Work* pwork;     // particle tiles (sim, tile), device
+    int npwork;
+    const Work* ywork;     // field-solver tiles, device
+    int nywork;
+    const int* simlist;    // device: indices into sims
+    int nsims;
+    int* counters;         // device: [0] push, [1] scatter, [2] field solver
+    int dim, prec;
+    size_t push_smem, yee_smem;
+    int push_grid, yee_grid, scatter_grid;
+};
+
+// per-step kernels (asynchronous)
+void launch_push(const Group& g, cudaStream_t s);
+void launch_scan(const Group& g, cudaStream_t s);
+void launch_scatter(const Group& g, cudaStream_t s);
+void launch_yee(const Group& g, cudaStream_t s);
+void launch_step_end(const Group& g, cudaStream_t s);
+
+// set-up: particles written linearly into buffer set 1, then sorted into set 0
+void launch_gen_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int slab_lo[3],
+                     const int slab_n[3], unsigned long long seed, double weight, cudaStream_t s);
+void launch_count_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s);
+void launch_sort_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s);
+void launch_scan_one(const SimDev* sim, int dim, int prec, cudaStream_t s);
+
+// diagnostics
+void launch_charge(const SimDev* sim, int dim, int prec, long long n_alive, double* rho, cudaStream_t s);
+void launch_gauss(const SimDev* sim, int dim, int prec, const int n[3], const double* rho, unsigned long long* out_bits,
+                  cudaStream_t s);
+void launch_energy_fields(const SimDev* sim, int dim, int prec, const int n[3], double* acc2, cudaStream_t s);
+void launch_energy_particles(const SimDev* sim, int dim, int prec, long long n_alive, long long n_exits,
+                             double* acc2, cudaStream_t s);
+void launch_histogram(const SimDev* sim, int dim, int prec, long long n_alive, long long n_exits, int n_e,
+                      double e_max, int n_a, double* bins, cudaStream_t s);
+void launch_eval_incident(const SimDev* sim, int dim, int prec, long long n, const double* pts, double* out,
+                          cudaStream_t s);
+
+// kernel attributes (dynamic shared memory opt-in); returns blocks per SM
+int prepare_push(int dim, int prec, size_t smem);
+int prepare_yee(int dim, int prec, size_t smem);
+int scatter_blocks_per_sm(int dim, int prec);
+
+}  // namespace sff

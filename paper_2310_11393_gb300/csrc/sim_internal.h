@@ -1,0 +1,60 @@
+// Host-side simulation handle shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/pic.h"
+#include "sff_common.cuh"
+#include "sff_kernels.h"
+
+using sff::Group;
+using sff::SimDev;
+using sff::Work;
+
+// bump allocator over one device allocation (256-byte aligned pieces)
+struct Arena {
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+    void* take(size_t bytes)
+    {
+        size_t off = (used + 255) & ~size_t(255);
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+struct GraphBundle {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct pic_sim {
+    pic_config cfg;
+    pic_params prm;
+    int device = 0;
+    int es = 4;                  // element size
+    SimDev h;                    // host copy of the descriptor
+    SimDev* d = nullptr;         // device descriptor
+    pic_allocator alloc{};
+    bool use_cuda_malloc = true;
+    Arena arena;
+    // single-simulation launch group
+    Group grp{};
+    Work* d_pwork = nullptr;
+    Work* d_ywork = nullptr;
+    int* d_list = nullptr;
+    int* d_counters = nullptr;
+    double* d_acc = nullptr;     // 8 doubles
+    unsigned long long* d_bits = nullptr;
+    GraphBundle step_graph;
+    cudaStream_t cap_stream = nullptr;
+    std::string err;
+    long long nalloc_tot = 0;    // na_x*na_y*na_z
+};
+
+
+// drop cached batch graphs that contain `s` (called by pic_destroy)
+void batch_forget(pic_sim* s);
