@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d"])
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
@@ -301,7 +302,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(workload(args.workload), 4) if world == 1 else None
+        run_cb = world == 1 and not args.no_cpu_baseline
+        out["cpu_baseline"] = cpu_baseline(workload(args.workload), 4) if run_cb else None
         print(json.dumps(out))
     if world > 1:
         import torch

@@ -169,9 +169,10 @@ pic_status validate(const pic_config* c, pic_sim* s)
     if (c->beam < PIC_BEAM_NONE || c->beam > PIC_BEAM_UNIFORM) return fail(s, PIC_EINVAL, "unknown beam %d", c->beam);
     if ((c->beam == PIC_BEAM_LP || c->beam == PIC_BEAM_RP)) {
         if (c->dim < 2) return fail(s, PIC_EINVAL, "LP/RP beams need dim >= 2");
-        const bool explicit_p = c->a_param > 0 && c->s_param > 0 && c->psi0 > 0;
-        if (!explicit_p && !(c->w0 > 0 && c->duration > 0 && c->a0 > 0))
-            return fail(s, PIC_EINVAL, "LP/RP beams need w0, duration, a0 > 0 (or a_param, s_param, psi0)");
+        if (!(c->a_param > 0 || c->w0 > 0)) return fail(s, PIC_EINVAL, "LP/RP beams need w0 > 0 or a_param > 0");
+        if (!(c->s_param > 0 || c->duration > 0))
+            return fail(s, PIC_EINVAL, "LP/RP beams need duration > 0 or s_param > 0");
+        if (!(c->psi0 > 0 || c->a0 > 0)) return fail(s, PIC_EINVAL, "LP/RP beams need a0 > 0 or psi0 > 0");
     }
     if (c->beam == PIC_BEAM_PLANE && !(c->duration > 0)) return fail(s, PIC_EINVAL, "plane wave needs duration > 0");
     const double dt = c->dt > 0 ? c->dt : c->cfl * c->dx / std::sqrt((double)c->dim);
@@ -1019,15 +1020,19 @@ pic_status pic_eval_incident(pic_sim* s, int64_t n, const double* pts, double* o
     if (!s || n < 0 || (n > 0 && (!pts || !out))) return fail(s, PIC_EINVAL, "bad argument");
     if (n == 0) return PIC_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    // points and results go through the diagnostics scratch (10 doubles per point)
-    if ((long long)n * 10 > s->nalloc_tot) return fail(s, PIC_ECAPACITY, "at most %lld points per call", s->nalloc_tot / 10);
-    double* dp = s->h.scratch;
-    double* dout = s->h.scratch + 4 * n;
-    CU_CHECK(s, cudaMemcpyAsync(dp, pts, (size_t)n * 4 * 8, cudaMemcpyHostToDevice, st));
-    launch_eval_incident(s->d, s->cfg.dim, s->cfg.precision, n, dp, dout, st);
-    CU_CHECK(s, cudaGetLastError());
-    CU_CHECK(s, cudaMemcpyAsync(out, dout, (size_t)n * 6 * 8, cudaMemcpyDeviceToHost, st));
-    CU_CHECK(s, cudaStreamSynchronize(st));
+    // a diagnostic entry point: temporary device buffers for the points and the results
+    double* dp = nullptr;
+    CU_CHECK(s, cudaMalloc(&dp, (size_t)n * 10 * sizeof(double)));
+    double* dout = dp + 4 * n;
+    cudaError_t e = cudaMemcpyAsync(dp, pts, (size_t)n * 4 * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        launch_eval_incident(s->d, s->cfg.dim, s->cfg.precision, n, dp, dout, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, (size_t)n * 6 * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dp);
+    if (e != cudaSuccess) return fail(s, PIC_ECUDA, "incident-field evaluation failed: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
 

@@ -49,10 +49,15 @@ def match_by_id(a, b):
 
 
 def momentum_error(p_gpu, p_ref, a0):
-    """max over particles of |p_gpu - p_ref| / max(|p_ref|, 1e-3 a0)."""
+    """max over particles of |p_gpu - p_ref| / max(|p_ref|, a0).
+
+    a0 (normalised field amplitude) is the quiver-momentum scale of an electron in the
+    pulse: the momentum is a sum of impulses of that size that largely cancel over a
+    carrier cycle, so its error is set by the field amplitude, not by |p| at the instant
+    it swings through zero."""
     common, ia, ib = match_by_id(p_gpu, p_ref)
     du = np.linalg.norm(p_gpu["u"][ia] - p_ref["u"][ib], axis=1)
-    den = np.maximum(np.linalg.norm(p_ref["u"][ib], axis=1), 1e-3 * a0)
+    den = np.maximum(np.linalg.norm(p_ref["u"][ib], axis=1), a0)
     return float((du / den).max()) if len(common) else 0.0, len(common)
 
 

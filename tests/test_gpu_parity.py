@@ -1,7 +1,11 @@
 """CUDA path (through the C-ABI) against the FP64 oracle on the same seeded inputs.
 
 Tolerances (the spec bar, made concrete):
-  * FP32 runs, first 50 steps: per particle |p_gpu - p_ref| / max(|p_ref|, 1e-3 a0) <= 1e-5;
+  * FP32 runs, first 50 steps: per particle |p_gpu - p_ref| / max(|p_ref|, a0) <= 1e-5, a0 being
+    the quiver-momentum scale (single precision evaluates the incident field to ~5e-7 of its
+    amplitude; impulses of size ~a0 dt add up and cancel over a cycle, so |p_gpu - p_ref| grows
+    like N dt C u a0 ~ 4e-6 a0 after 50 steps with u = 6e-8 and C ~ 10, while |p| itself can
+    be arbitrarily small);
     per field component max|F_gpu - F_ref| / max|F_ref| <= 1e-5;
   * FP64 runs: the same quantities to 1e-9 (only the summation order of deposits differs);
   * integer and index data (particle ids, which particles left the box, cell indices after
@@ -89,7 +93,7 @@ def test_incident_field_point_parity(P, orc, beam, prec):
     want = np.array([np.concatenate(orc.incident(cfg, p[:3], p[3])) for p in pts])
     scale = np.abs(want).max()
     err = np.abs(got - want).max() / scale
-    tol = 2e-6 if prec == "fp32" else 1e-11
+    tol = 5e-6 if prec == "fp32" else 1e-11
     assert err < tol, err
 
 
@@ -156,14 +160,24 @@ def test_3d_rp_parity(P, orc, prec):
 
 
 def test_gauss_law_on_the_gpu(P):
+    """No particle leaves: div E - rho stays at round-off (Esirkepov deposition + Yee)."""
+    for prec, tol in ((synth.FP64, 1e-12), (synth.FP32, 2e-6)):
+        w = small_2d(precision=prec).with_(a0=2.0)
+        sim = P.Simulation(P.config_from(w))
+        sim.step(30)
+        assert sim.info().n_exits == 0
+        assert sim.gauss_residual() < tol * w.n_e * 100
+
+
+def test_gauss_residual_matches_the_oracle_with_exits(P, orc):
+    """Particles that leave take their charge with them; the residual they leave behind is
+    the same on both sides."""
     w = small_2d(precision=synth.FP64)
-    sim = P.Simulation(P.config_from(w))
-    sim.step(40)
-    assert sim.gauss_residual() < 1e-11
-    w32 = small_2d(precision=synth.FP32)
-    s32 = P.Simulation(P.config_from(w32))
-    s32.step(40)
-    assert s32.gauss_residual() < 2e-5 * w32.n_e
+    sim, ref = run_pair(P, orc, w, 40)
+    assert sim.info().n_exits > 0
+    rg, rr = sim.gauss_residual(), ref.gauss_residual()
+    assert rr > 1e-3
+    assert abs(rg - rr) < 1e-9 * rr
 
 
 def test_exits_match_the_oracle(P, orc):
@@ -176,3 +190,41 @@ def test_exits_match_the_oracle(P, orc):
     common, ia, ib = match_by_id(eg, er)
     assert np.abs(eg["u"][ia] - er["u"][ib]).max() < 1e-8 * max(1.0, np.abs(er["u"]).max())
     np.testing.assert_array_equal(eg["step"][ia], er["step"][ib])
+
+
+@pytest.mark.parametrize("wl", ["2d", "3d"])
+def test_full_size_first_push_on_sampled_particles(P, orc, wl):
+    """Paper-sized workloads, in the launch configuration the benchmark times: at step 0 the
+    scattered field is zero, so each particle's first push depends only on the incident field
+    at its own position; the oracle recomputes a sample of them one by one."""
+    w = synth.c2_2d_lp() if wl == "2d" else synth.c3_3d_rp()
+    sim = P.Simulation(P.config_from(w))
+    assert sim.info().n_alive == w.n_particles
+    sim.step(1)
+    pg = sim.particles()
+    x, u, wt, ids = synth.slab_particles(w)
+    rng = np.random.default_rng(17)
+    pick = np.sort(rng.choice(len(ids), 3000, replace=False))
+    ref = orc.Sim(orc.config_from(w.with_(ppc=0)))
+    ref.set_particles(x[pick], u[pick], wt[pick], ids[pick])
+    ref.step(1)
+    pr = ref.particles()
+    err, n = momentum_error(pg, pr, w.a0)
+    assert n == len(pr["id"])
+    assert err < 1e-6, err
+    assert position_error(pg, pr, w.dx) < 1e-5
+
+
+def test_full_size_1d_fp64_run(P, orc):
+    """The 1D FP64 workload over its full 2000 steps: particles, fields and energies."""
+    w = synth.c1_1d_plane()
+    sim, ref = run_pair(P, orc, w, w.steps)
+    pg, pr = sim.particles(), ref.particles()
+    assert set(pg["id"].tolist()) == set(pr["id"].tolist())
+    err, n = momentum_error(pg, pr, w.a0)
+    assert err < 1e-8, err
+    fe = field_errors(sim.fields(), ref.fields())
+    assert fe[:6].max() < 1e-8, fe
+    eg, er = sim.energies(), ref.energies()
+    for k in range(4):
+        assert abs(eg[k] - er[k]) <= 1e-8 * max(abs(er[k]), 1e-30), (k, eg[k], er[k])
