@@ -37,11 +37,11 @@ UNIT = "pushes/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (default: the workload's full run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d"])
-    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--profile-steps", type=int, default=0, help="steps timed kernel by kernel (default: --steps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -116,14 +116,16 @@ class Clocks:
 
 
 def flops_per_push(w):
-    """Algorithmic FP32 operations of one push of the 2D/3D LP/RP path (counted from the formulas
-    the kernel evaluates; an FMA counts 2, a transcendental call counts 1)."""
+    """Algorithmic FP32 operations of one push (add/mul = 1, FMA = 2, each transcendental call = 1),
+    counted from the formulas the kernel evaluates, with BOTH terms tau_+ and tau_- of the
+    closed form evaluated (the kernel drops a term below e^-36 of the peak; that saving is not
+    subtracted, so the fraction reported is an upper bound of the pipe use)."""
     D = w.dim
-    gather = 6 * (2 * 3 ** D) + D * 2 * 8                      # 3^D-point stencils, shape weights
+    gather = {1: 6 * 6 + 12, 2: 6 * 24 + 24, 3: 6 * 78 + 36}[D]
     boris = 60
-    deposit = {1: 40, 2: 220, 3: 1100}[D]
-    incident = {synth.BEAM_LP: 560, synth.BEAM_RP: 540, synth.BEAM_PLANE: 20}.get(w.beam, 0)
-    move = 10 * D
+    deposit = {1: 40, 2: 350, 3: 1700}[D]
+    incident = {synth.BEAM_LP: 280, synth.BEAM_RP: 270, synth.BEAM_PLANE: 25}.get(w.beam, 0)
+    move = 5 * D
     return gather + boris + deposit + incident + move
 
 
@@ -149,8 +151,13 @@ def run_ours(args, rank, world, local_rank):
     cfg = pic.config_from(w)
     stream = torch.cuda.current_stream(dev).cuda_stream
     alloc = pic.torch_allocator(local_rank)
+    # warm-up: W steps on a throw-away instance (clocks, caches, graph, launch attributes)
+    warm = pic.Simulation(cfg, allocator=alloc, stream=stream)
+    warm.step(args.warmup)
+    torch.cuda.synchronize()
+    warm.close()
+    # the job: a fresh simulation (inputs resident in HBM) advanced K steps from t = 0
     sim = pic.Simulation(cfg, allocator=alloc, stream=stream)
-    sim.step(args.warmup)
     torch.cuda.synchronize()
     n_a = sim.info().n_alive
     if world > 1:
@@ -178,16 +185,30 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(p)
         tot_pushes = float(p.item())
         torch.distributed.barrier()
-    # live per-kernel timing of the same workload (events between the kernels of a step)
-    prof = pic.pic_profile_step(sim.h, args.profile_steps, stream)
-    n_c = sim.info().n_alive
-    push_s = prof[0] / args.profile_steps
-    yee_s = prof[3] / args.profile_steps
     info = sim.info()
     sim.close()
+    # live per-kernel timing over the same window: another fresh instance, K steps from t = 0,
+    # CUDA events between the kernels of every step
+    psim = pic.Simulation(cfg, allocator=alloc, stream=stream)
+    nsteps_prof = args.steps if args.profile_steps <= 0 else min(args.steps, args.profile_steps)
+    nwin = 10 if nsteps_prof >= 10 else 1
+    prof = np.zeros(5)
+    windows = []
+    done = 0
+    for k in range(nwin):
+        m = nsteps_prof * (k + 1) // nwin - done
+        pw = pic.pic_profile_step(psim.h, m, stream)
+        prof += pw
+        windows.append({"steps": [done, done + m], "n_alive": int(psim.info().n_alive),
+                        "ms_per_step": [round(x / m * 1e3, 4) for x in pw]})
+        done += m
+    n_c = psim.info().n_alive
+    psim.close()
+    push_s = prof[0] / nsteps_prof
+    yee_s = prof[3] / nsteps_prof
 
     hbm, sm_max, src = peaks()
-    npush = 0.5 * (n_b + n_c)
+    npush = 0.5 * (n_a + n_c)
     fl = flops_per_push(w) * npush
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s: SMs x FP32 lanes x FMA x clock
     alu_frac = fl / push_s / 1e12 / fp32_peak
@@ -205,7 +226,9 @@ def run_ours(args, rank, world, local_rank):
                          "bytes_per_push": round(bytes_per_push(w), 2)},
             "yee": {"ms": round(yee_s * 1e3, 4), "achieved_gbs": round(yee_bytes / yee_s / 1e9, 1),
                     "frac_of_hbm": round(yee_bytes / yee_s / 1e9 / hbm, 4), "bytes_per_cell": 18 * es},
-            "phases_ms": [round(x / args.profile_steps * 1e3, 4) for x in prof]}
+            "phases_ms": [round(x / nsteps_prof * 1e3, 4) for x in prof],
+            "phases": ["push+deposit", "tile scan", "scatter", "field solve", "step end"],
+            "windows": windows}
 
     e2e = None
     if not args.no_e2e:
@@ -288,6 +311,8 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.steps <= 0:
+        args.steps = workload(args.workload).steps
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -15,8 +15,9 @@
 // Psi z^ (E = grad d_z Psi - d_tt Psi z^, B = d_t curl Psi z^) for RP.  This is the
 // paper's expansion regrouped (sin^2(theta)/R^3 = rho^2/R^5 etc.), so nothing divides by r.
 //
-// Precision: the phase-critical differences t - z and t + z are formed in double from
-// the particle's integer cell and offset before anything is rounded to R; the choice of
+// Precision: the phase-critical differences t - z and t + z are formed in double once per
+// reference cell and carried as hi + lo pairs (see PhaseRef), so the particle loop has no
+// double-precision arithmetic and no cancellation beyond the final rounding; the choice of
 // the square-root branch (Re(R conj(zeta+i)) >= 0, allowed because Phi is even in R)
 // and aR - (z+ia) = a rho^2/(R + zeta + i) remove the remaining cancellations.  Near the
 // ring u = 0, where the terms above cancel, Phi is summed as its power series in u:
@@ -28,21 +29,15 @@
 
 namespace sff {
 
+// Incident-field constants (host side, at set-up) from the descriptor's double values.
 template <typename R>
-struct BeamC {
-    int beam, envelope;
-    R a, two_a, s, inv_s, sp1, sp2, k, phi0, ring2;   // ring2 = delta^4: series when |u|^2 < delta^4
-    R a0, dur, inv_dur, t_c, xic;                     // plane wave
-    R eu[3], bu[3];
-};
-
-template <typename R>
-__device__ __forceinline__ BeamC<R> beam_consts(const SimDev& S)
+inline BeamC<R> make_beam_consts(const SimDev& S)
 {
     BeamC<R> b;
     b.beam = S.beam;
     b.envelope = S.envelope;
     b.a = R(S.a);
+    b.inv_a = R(S.a > 0 ? 1.0 / S.a : 0.0);
     b.two_a = R(2.0 * S.a);
     b.s = R(S.s);
     b.inv_s = R(S.s > 0 ? 1.0 / S.s : 0.0);
@@ -56,7 +51,7 @@ __device__ __forceinline__ BeamC<R> beam_consts(const SimDev& S)
     b.dur = R(S.duration);
     b.inv_dur = R(S.duration > 0 ? 1.0 / S.duration : 0.0);
     b.t_c = R(S.t_focus);
-    b.xic = R(S.envelope == 1 ? S.t_focus : S.duration);
+    b.dxr = R(S.dx);
     for (int d = 0; d < 3; ++d) {
         b.eu[d] = R(S.e_unif[d]);
         b.bu[d] = R(S.b_unif[d]);
@@ -64,15 +59,32 @@ __device__ __forceinline__ BeamC<R> beam_consts(const SimDev& S)
     return b;
 }
 
-// e^{i phi0} w^{-(s+1)}, w = 1 - i tau/s, and g^(1), g^(2) (Eq. poisson_dstr)
+// log|w|, w = 1 - i tau/s (decides whether the term matters at all)
 template <typename R>
-__device__ __forceinline__ void poisson3(const BeamC<R>& b, Cx<R> tau, Cx<R>& g0, Cx<R>& g1, Cx<R>& g2)
+__device__ __forceinline__ R log_abs_w(const BeamC<R>& b, Cx<R> tau)
 {
     const R ti = tau.y * b.inv_s, tr = tau.x * b.inv_s;
-    const Cx<R> w = {R(1) + ti, -tr};
-    const R lnw = R(0.5) * m_log1p(ti * (R(2) + ti) + tr * tr);   // log|w|
+    return R(0.5) * m_log1p(ti * (R(2) + ti) + tr * tr);
+}
+
+// |w|^{-(s+1)} below e^{-36}: the term is below ~1e-11 of the peak field even after the
+// largest 1/R^5 and polynomial factors the closed form applies, so it is dropped
+template <typename R>
+__device__ __forceinline__ bool negligible(const BeamC<R>& b, R lnw)
+{
+    return b.sp1 * lnw > R(36);
+}
+
+__device__ __forceinline__ float m_exp_mag(float x) { return __expf(x); }   // error matters only near x = 0
+__device__ __forceinline__ double m_exp_mag(double x) { return exp(x); }
+
+// e^{i phi0} w^{-(s+1)}, w = 1 - i tau/s, and g^(1), g^(2) (Eq. poisson_dstr), given log|w|
+template <typename R>
+__device__ __forceinline__ void poisson3(const BeamC<R>& b, Cx<R> tau, R lnw, Cx<R>& g0, Cx<R>& g1, Cx<R>& g2)
+{
+    const Cx<R> w = {R(1) + tau.y * b.inv_s, -tau.x * b.inv_s};
     const R th = m_atan2(w.y, w.x);
-    const R mag = m_exp(-b.sp1 * lnw);
+    const R mag = m_exp_mag(-b.sp1 * lnw);
     R sn, cs;
     m_sincos(b.phi0 - b.sp1 * th, &sn, &cs);
     g0 = {mag * cs, mag * sn};
@@ -89,6 +101,10 @@ __device__ __noinline__ void phi_series(const BeamC<R>& b, Cx<R> u, R trel, Cx<R
 {
     const Cx<R> w0 = {R(1) + b.a * b.inv_s, -trel * b.inv_s};      // 1 - i(trel + i a)/s
     R lnw = R(0.5) * m_log1p((w0.x * w0.x + w0.y * w0.y) - R(1));
+    if (negligible(b, lnw)) {
+        P[0] = P[1] = P[2] = P[3] = Cx<R>{R(0), R(0)};
+        return;
+    }
     R th = m_atan2(w0.y, w0.x);
     R mag = m_exp(-b.sp1 * lnw);
     R sn, cs;
@@ -158,9 +174,19 @@ __device__ __forceinline__ void focused_field(const BeamC<R>& b, R xi, R eta, R 
         const Cx<R> qq = (b.a * rho2) * cinv(den);     // a R - (z + i a)
         const Cx<R> taum = {tmz - qq.x, -qq.y};
         const Cx<R> taup = {tpz + qq.x, b.two_a + qq.y};
-        Cx<R> g0m, g1m, g2m, g0p, g1p, g2p;
-        poisson3(b, taum, g0m, g1m, g2m);
-        poisson3(b, taup, g0p, g1p, g2p);
+        const R lnm = log_abs_w(b, taum), lnp = log_abs_w(b, taup);
+        const bool use_m = !negligible(b, lnm), use_p = !negligible(b, lnp);
+        if (!use_m && !use_p) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                E[d] = R(0);
+                B[d] = R(0);
+            }
+            return;
+        }
+        Cx<R> g0m = {0, 0}, g1m = {0, 0}, g2m = {0, 0}, g0p = {0, 0}, g1p = {0, 0}, g2p = {0, 0};
+        if (use_m) poisson3(b, taum, lnm, g0m, g1m, g2m);
+        if (use_p) poisson3(b, taup, lnp, g0p, g1p, g2p);
         const Cx<R> G0m = g0p - g0m, G1p = g1p + g1m, G1m = g1p - g1m, G2p = g2p + g2m, G2m = g2p - g2m;
         const Cx<R> iR = cinv(Rr);
         const Cx<R> iR2 = iR * iR;
@@ -195,47 +221,97 @@ __device__ __forceinline__ void focused_field(const BeamC<R>& b, R xi, R eta, R 
     }
 }
 
-// Position of a particle in grid coordinates: cell index c and offset o per axis.
-// Returns the incident E, B (grid axes) at time t = step*dt.
+// Phase-critical x-differences, formed once per reference cell x0 in double precision and
+// carried as unevaluated sums hi + lo of two R numbers.  For a particle at cell x0 + lx with
+// offset o, x - x(x0) = lx dx_h + (o dx + lx dx_l), where dx_h keeps 12 significant bits so
+// that lx dx_h is exact; then t - z = ((A_h - lx dx_h) + A_l) - (o dx + lx dx_l) has no
+// cancellation beyond the final rounding, without any double-precision work per particle.
+template <typename R>
+struct PhaseRef {
+    int x0;
+    R ah, al;      // LP/RP: t_rel - Z(x0);  plane: xi(x0) - xi_c + phi0 (carrier phase)
+    R bh, bl;      // LP/RP: t_rel + Z(x0);  plane: xi(x0) = t - (x(x0) - x_ref)
+    R zh, zl;      // Z(x0) = x(x0) - focus_x
+    R dxh, dxl, dxr;
+    R trel;
+};
+
+template <typename R>
+__device__ __forceinline__ void split_hl(double v, R& h, R& l)
+{
+    h = R(v);
+    l = R(v - (double)h);
+}
+
+template <typename R>
+__device__ __forceinline__ PhaseRef<R> phase_ref(const SimDev& S, double t, int x0)
+{
+    PhaseRef<R> p;
+    p.x0 = x0;
+    const double Z0 = (double)x0 * S.dx - S.focus[0];
+    double A, Bv;
+    if (S.beam == BEAM_PLANE) {
+        const double xi0 = t - Z0;
+        A = xi0 - (S.envelope == 1 ? S.t_focus : S.duration) + S.phi0;
+        Bv = xi0;
+        p.trel = R(0);
+    } else {
+        const double trel = t - S.t_focus;
+        A = trel - Z0;
+        Bv = trel + Z0;
+        p.trel = R(trel);
+    }
+    split_hl(A, p.ah, p.al);
+    split_hl(Bv, p.bh, p.bl);
+    split_hl(Z0, p.zh, p.zl);
+    const double dh = (double)__int_as_float(__float_as_int((float)S.dx) & (int)0xFFFFF000);
+    p.dxh = R(dh);
+    p.dxl = R(S.dx - dh);
+    p.dxr = R(S.dx);
+    return p;
+}
+
+// Incident E, B (grid axes) at a particle in cell c with offsets o, at the time of `pr`.
 template <int D, typename R>
-__device__ __forceinline__ void incident_at(const SimDev& S, const BeamC<R>& b, const int c[3], const R o[3],
-                                            double t, R E[3], R B[3])
+__device__ __forceinline__ void incident_at(const SimDev& S, const BeamC<R>& b, const PhaseRef<R>& pr, const int c[3],
+                                            const R o[3], R E[3], R B[3])
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         E[d] = R(0);
         B[d] = R(0);
     }
-    if (b.beam == BEAM_PLANE) {
-        // xi = t - (x - x_ref), formed in double
-        const double x = fma((double)c[0] + (double)o[0], S.dx, -S.focus[0]);
-        const double xi_d = t - x;
-        const R xi = R(xi_d);
-        const R arg = R(xi_d - (double)b.xic + (double)b.phi0);
-        R env;
-        if (b.envelope == 1) {
-            const R v = (xi - b.t_c) * b.inv_dur;
-            env = m_exp2(R(-4) * v * v);
-        } else {
-            if (xi <= R(0) || xi >= R(2) * b.dur) return;
-            const R sn = m_sinpi(xi * R(0.5) * b.inv_dur);
-            env = sn * sn;
+    if (b.beam == BEAM_PLANE || b.beam == BEAM_LP || b.beam == BEAM_RP) {
+        const R lx = R(c[0] - pr.x0);
+        const R sh = lx * pr.dxh;                       // exact
+        const R sl = o[0] * pr.dxr + lx * pr.dxl;
+        if (b.beam == BEAM_PLANE) {
+            const R xi = ((pr.bh - sh) + pr.bl) - sl;
+            const R arg = ((pr.ah - sh) + pr.al) - sl;
+            R env;
+            if (b.envelope == 1) {
+                const R v = (xi - b.t_c) * b.inv_dur;
+                env = m_exp2(R(-4) * v * v);
+            } else {
+                if (xi <= R(0) || xi >= R(2) * b.dur) return;
+                const R sn = m_sinpi(xi * R(0.5) * b.inv_dur);
+                env = sn * sn;
+            }
+            const R f = b.a0 * m_sin(arg) * env;
+            E[1] = f;
+            B[2] = f;
+            return;
         }
-        const R f = b.a0 * m_sin(arg) * env;
-        E[1] = f;
-        B[2] = f;
-    } else if (b.beam == BEAM_LP || b.beam == BEAM_RP) {
         // beam frame: paper z = grid x, paper x = grid y, paper y = grid z
-        const double Zd = fma((double)c[0] + (double)o[0], S.dx, -S.focus[0]);
-        const double trel = t - S.t_focus;
-        const R tmz = R(trel - Zd), tpz = R(trel + Zd);
-        const R inv_a = R(1.0 / S.a);
-        const R zeta = R(Zd) * inv_a;
+        const R tmz = ((pr.ah - sh) + pr.al) - sl;
+        const R tpz = ((pr.bh + sh) + pr.bl) + sl;
+        const R inv_a = b.inv_a;
+        const R zeta = ((pr.zh + sh) + (pr.zl + sl)) * inv_a;
         R xi = R(0), eta = R(0);
-        if constexpr (D >= 2) xi = ((R)(c[1] - S.icf[1]) + (o[1] - R(S.frf[1]))) * R(S.dx) * inv_a;
-        if constexpr (D >= 3) eta = ((R)(c[2] - S.icf[2]) + (o[2] - R(S.frf[2]))) * R(S.dx) * inv_a;
+        if constexpr (D >= 2) xi = ((R)(c[1] - S.icf[1]) + (o[1] - R(S.frf[1]))) * (b.dxr * inv_a);
+        if constexpr (D >= 3) eta = ((R)(c[2] - S.icf[2]) + (o[2] - R(S.frf[2]))) * (b.dxr * inv_a);
         R Ep[3], Bp[3];
-        focused_field<R>(b, xi, eta, zeta, tmz, tpz, R(trel), Ep, Bp);
+        focused_field<R>(b, xi, eta, zeta, tmz, tpz, pr.trel, Ep, Bp);
         E[0] = Ep[2];
         E[1] = Ep[0];
         E[2] = Ep[1];

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/pic.h"
+#include "beam.cuh"
 #include "sff_common.cuh"
 #include "sff_kernels.h"
 #include "sim_internal.h"
@@ -556,6 +557,8 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     h.psi0 = prm.psi0;
     h.max_exits = L.max_exits;
     h.cap = L.cap;
+    h.bcf = make_beam_consts<float>(h);
+    h.bcd = make_beam_consts<double>(h);
     // tensor maps (every box extent must stay within TMA's 256 elements per dimension)
     for (int d = 0; d < 3; ++d)
         if (L.pb[d] > 256 || L.yb[d] > 256) {

@@ -100,7 +100,7 @@ __global__ void k_energy_fields(const SimDev* __restrict__ sim, int m0, int m1, 
     const int par = S.st->parity;
     const long long eb = (long long)comp_eb(par) * S.sc;
     const double t = (double)S.st->step * S.dt;
-    const BeamC<R> bc = beam_consts<R>(S);
+    const BeamC<R>& bc = beam_of<R>(S);
     const long long total = (long long)m0 * m1 * m2;   // extents n+1 on resolved axes
     double es = 0.0, et = 0.0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
@@ -126,7 +126,8 @@ __global__ void k_energy_fields(const SimDev* __restrict__ sim, int m0, int m1, 
             double inc = 0.0;
             if (S.beam != BEAM_NONE) {
                 R Ei[3], Bi[3];
-                incident_at<D, R>(S, bc, cc, oo, t, Ei, Bi);
+                const PhaseRef<R> pr = phase_ref<R>(S, t, cc[0]);
+                incident_at<D, R>(S, bc, pr, cc, oo, Ei, Bi);
                 inc = comp < 3 ? (double)Ei[c] : (double)Bi[c];
             }
             et += 0.5 * (f + inc) * (f + inc);
@@ -209,7 +210,7 @@ __global__ void k_eval_incident(const SimDev* __restrict__ sim, long long n, con
                                 double* __restrict__ out)
 {
     const SimDev& S = *sim;
-    const BeamC<R> bc = beam_consts<R>(S);
+    const BeamC<R>& bc = beam_of<R>(S);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         int c[3] = {0, 0, 0};
@@ -221,7 +222,8 @@ __global__ void k_eval_incident(const SimDev* __restrict__ sim, long long n, con
             o[d] = R(X - fl);
         }
         R E[3], B[3];
-        incident_at<D, R>(S, bc, c, o, pts[4 * p + 3], E, B);
+        const PhaseRef<R> pr = phase_ref<R>(S, pts[4 * p + 3], c[0]);
+        incident_at<D, R>(S, bc, pr, c, o, E, B);
         for (int d = 0; d < 3; ++d) {
             out[6 * p + d] = (double)E[d];
             out[6 * p + 3 + d] = (double)B[d];

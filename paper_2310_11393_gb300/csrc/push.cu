@@ -97,13 +97,14 @@ __device__ __forceinline__ void sm_add(double* a, double v)
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) k_push(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_push(const SimDev* __restrict__ sims, const Work* __restrict__ work,
                                               int nwork, int* __restrict__ counter)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item;
     __shared__ int s_hist[27];
+    __shared__ PhaseRef<R> s_pref;
     const int tid = threadIdx.x, nth = blockDim.x;
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -147,6 +148,8 @@ __global__ void __launch_bounds__(256) k_push(const SimDev* __restrict__ sims, c
             tensormap_acquire(&S.tm_pj);
             mbar_arrive_expect_tx(&bar, (unsigned)(6 * bvol * sizeof(R)));
             tma_load_box<D>(Fs, &S.tm_pf, org, comp_eb(par), &bar);
+            // double-precision phase reference of this tile, once per tile
+            s_pref = phase_ref<R>(S, (double)st->step * S.dt, T0[0]);
         }
         for (int i = tid; i < 3 * bvol; i += nth) Js[i] = R(0);
         if (tid < 27) s_hist[tid] = 0;
@@ -161,8 +164,8 @@ __global__ void __launch_bounds__(256) k_push(const SimDev* __restrict__ sims, c
             return;
         }
 
-        const BeamC<R> bc = beam_consts<R>(S);
-        const double t = (double)st->step * S.dt;
+        const BeamC<R>& bc = beam_of<R>(S);
+        const PhaseRef<R> pref = s_pref;
         const R dt = R(S.dt);
         const R dtdx = R(S.dt * S.inv_dx);
         const R jfac = R(S.dx / S.dt);              // -q dx/dt, q = -1
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(256) k_push(const SimDev* __restrict__ sims, c
             // ---- incident field at (x^n, t^n) ----
             {
                 R Ei[3], Bi[3];
-                incident_at<D, R>(S, bc, c, o, t, Ei, Bi);
+                incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     E[d] += Ei[d];

@@ -30,6 +30,16 @@ struct DevState {
     long long pad[5];
 };
 
+// Incident-field constants in the working precision R, computed on the host at set-up.
+template <typename R>
+struct BeamC {
+    int beam, envelope;
+    R a, inv_a, two_a, s, inv_s, sp1, sp2, k, phi0, ring2;   // ring2 = delta^4: series when |u|^2 < delta^4
+    R a0, dur, inv_dur, t_c;                                  // plane wave
+    R dxr;                                                    // cell size
+    R eu[3], bu[3];
+};
+
 // Everything a kernel needs to know about one simulation.  Lives in device memory
 // (an array of these serves a batch); tensor maps must stay 64-byte aligned.
 struct alignas(128) SimDev {
@@ -75,12 +85,22 @@ struct alignas(128) SimDev {
     DevState* st;
     double* rho_ion;          // [na_z][na_y][na_x] ion charge density (diagnostics)
     double* scratch;          // diagnostics scratch: charge density, same layout
+    BeamC<float> bcf;         // incident-field constants for the FP32 kernels
+    BeamC<double> bcd;        // ... and the FP64 kernels
 };
+
+template <typename R>
+__device__ __forceinline__ const BeamC<R>& beam_of(const SimDev& S)
+{
+    if constexpr (sizeof(R) == 4) return S.bcf;
+    else return S.bcd;
+}
 
 struct Work {
     int sim;
     int tile;
 };
+
 
 // ---------------------------------------------------------------------------------
 // inline PTX: shared-memory addresses, mbarrier, TMA

