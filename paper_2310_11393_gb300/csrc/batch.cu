@@ -56,16 +56,15 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
     for (auto& kv : by) {
         const std::vector<int>& mem = kv.second;
         const int n = (int)mem.size();
-        long long npw = 0, nyw = 0;
+        long long nyw = 0, nch = 0;
         size_t psm = 0, ysm = 0;
         for (int i : mem) {
-            npw += sims[i]->h.nptiles;
             nyw += sims[i]->h.nytiles;
+            nch += sims[i]->h.max_chunks;
             psm = std::max(psm, sims[i]->grp.push_smem);
             ysm = std::max(ysm, sims[i]->grp.yee_smem);
         }
-        const size_t bytes = a256(sizeof(SimDev) * n) + a256(sizeof(Work) * npw) + a256(sizeof(Work) * nyw) +
-                             a256(sizeof(int) * n) + a256(64);
+        const size_t bytes = a256(sizeof(SimDev) * n) + a256(sizeof(Work) * nyw) + a256(sizeof(int) * (n + 1)) + a256(64);
         GroupRes gr;
         if (cudaMalloc(&gr.mem, bytes) != cudaSuccess) {
             err = "batch descriptor allocation failed";
@@ -75,38 +74,29 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         char* p = (char*)gr.mem;
         SimDev* d_sims = (SimDev*)p;
         p += a256(sizeof(SimDev) * n);
-        Work* d_pw = (Work*)p;
-        p += a256(sizeof(Work) * npw);
         Work* d_yw = (Work*)p;
         p += a256(sizeof(Work) * nyw);
-        int* d_list = (int*)p;
-        p += a256(sizeof(int) * n);
+        int* d_gp = (int*)p;
+        p += a256(sizeof(int) * (n + 1));
         int* d_cnt = (int*)p;
         std::vector<SimDev> hs(n);
-        std::vector<Work> pw, yw;
-        std::vector<int> list(n);
-        pw.reserve(npw);
+        std::vector<Work> yw;
         yw.reserve(nyw);
         for (int k = 0; k < n; ++k) {
             pic_sim* s = sims[mem[k]];
             hs[k] = s->h;
-            list[k] = k;
-            for (int t = 0; t < s->h.nptiles; ++t) pw.push_back({k, t});
             for (int t = 0; t < s->h.nytiles; ++t) yw.push_back({k, t});
         }
         cudaMemcpy(d_sims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice);
-        cudaMemcpy(d_pw, pw.data(), sizeof(Work) * npw, cudaMemcpyHostToDevice);
         cudaMemcpy(d_yw, yw.data(), sizeof(Work) * nyw, cudaMemcpyHostToDevice);
-        cudaMemcpy(d_list, list.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+        cudaMemset(d_gp, 0, sizeof(int) * (n + 1));
         cudaMemset(d_cnt, 0, 64);
         Group& g = gr.g;
         g.sims = d_sims;
-        g.pwork = d_pw;
-        g.npwork = (int)npw;
+        g.nsims = n;
+        g.gprefix = d_gp;
         g.ywork = d_yw;
         g.nywork = (int)nyw;
-        g.simlist = d_list;
-        g.nsims = n;
         g.counters = d_cnt;
         g.dim = kv.first.first;
         g.prec = kv.first.second;
@@ -116,9 +106,9 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         const int bp = std::max(1, sff::prepare_push(g.dim, g.prec, psm));
         const int byy = std::max(1, sff::prepare_yee(g.dim, g.prec, ysm));
         const int bs = std::max(1, sff::scatter_blocks_per_sm(g.dim, g.prec));
-        g.push_grid = (int)std::max<long long>(1, std::min<long long>(npw, (long long)bp * nsm));
+        g.push_grid = (int)std::max<long long>(1, std::min<long long>(nch, (long long)bp * nsm));
         g.yee_grid = (int)std::max<long long>(1, std::min<long long>(nyw, (long long)byy * nsm));
-        g.scatter_grid = (int)std::max<long long>(1, std::min<long long>(npw, (long long)bs * nsm));
+        g.scatter_grid = (int)std::max<long long>(1, std::min<long long>(nch, (long long)bs * nsm));
         e->groups.push_back(gr);
     }
     if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess ||
@@ -128,6 +118,7 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         return PIC_ECUDA;
     }
     for (auto& gr : e->groups) {
+        sff::launch_prefix(gr.g, e->cs);
         sff::launch_push(gr.g, e->cs);
         sff::launch_scan(gr.g, e->cs);
         sff::launch_scatter(gr.g, e->cs);

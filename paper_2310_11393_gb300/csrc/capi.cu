@@ -154,6 +154,7 @@ struct Layout {
     long long sy, sz, sc, natot;
     int nptiles, nytiles;
     long long cap, max_exits, nslab;
+    int chunk, max_chunks;
     size_t push_smem, yee_smem;
     size_t bytes;
 };
@@ -255,6 +256,8 @@ Layout make_layout(const pic_config* c)
     }
     L.cap = c->max_particles > 0 ? c->max_particles : std::max<long long>(L.nslab, 1);
     L.max_exits = c->max_exits > 0 ? c->max_exits : L.cap;
+    L.chunk = 2048;
+    L.max_chunks = (int)(L.nptiles + (L.cap + L.chunk - 1) / L.chunk + 1);
     const long long pbv = (long long)L.pb[0] * L.pb[1] * L.pb[2];
     const long long ybv = (long long)L.yb[0] * L.yb[1] * L.yb[2];
     const long long ytv = (long long)L.yt[0] * L.yt[1] * L.yt[2];
@@ -269,10 +272,11 @@ Layout make_layout(const pic_config* c)
         b += align256(L.cap * L.es) * (size_t)(c->dim + 4);            // off, mom, w
     }
     (void)per;
-    b += 2 * align256((size_t)(L.nptiles + 1) * 4) + 2 * align256((size_t)L.nptiles * 4);
+    b += 4 * align256((size_t)(L.nptiles + 1) * 4) + 2 * align256((size_t)L.nptiles * 4);
+    b += 2 * align256((size_t)L.max_chunks * 4);
     b += align256((size_t)L.max_exits * EXIT_DOUBLES * 8);
     b += 2 * align256((size_t)L.natot * 8);
-    b += align256((size_t)L.nptiles * sizeof(Work)) + align256((size_t)L.nytiles * sizeof(Work));
+    b += align256((size_t)L.nytiles * sizeof(Work));
     b += align256(64) + align256(64) + align256(8 * 8) + align256(8);
     L.bytes = b;
     return L;
@@ -372,6 +376,7 @@ pic_status capture_step(pic_sim* s)
 {
     cudaStream_t cs = s->cap_stream;
     CU_CHECK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    launch_prefix(s->grp, cs);
     launch_push(s->grp, cs);
     launch_scan(s->grp, cs);
     launch_scatter(s->grp, cs);
@@ -510,14 +515,19 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     }
     h.toff[0] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
     h.toff[1] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
+    h.coff[0] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
+    h.coff[1] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
+    h.ctile[0] = (int*)A.take((size_t)L.max_chunks * 4);
+    h.ctile[1] = (int*)A.take((size_t)L.max_chunks * 4);
+    h.chunk = L.chunk;
+    h.max_chunks = L.max_chunks;
     h.tcnt = (int*)A.take((size_t)L.nptiles * 4);
     h.tcur = (int*)A.take((size_t)L.nptiles * 4);
     h.exits = (double*)A.take((size_t)L.max_exits * EXIT_DOUBLES * 8);
     h.rho_ion = (double*)A.take((size_t)L.natot * 8);
     h.scratch = (double*)A.take((size_t)L.natot * 8);
-    s->d_pwork = (Work*)A.take((size_t)L.nptiles * sizeof(Work));
     s->d_ywork = (Work*)A.take((size_t)L.nytiles * sizeof(Work));
-    s->d_list = (int*)A.take(64);
+    s->d_gprefix = (int*)A.take(64);
     s->d_counters = (int*)A.take(64);
     s->d_acc = (double*)A.take(64);
     s->d_bits = (unsigned long long*)A.take(8);
@@ -592,6 +602,8 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     INIT_CHECK(cudaMemsetAsync(h.F, 0, (size_t)NFCOMP * L.natot * L.es, st));
     INIT_CHECK(cudaMemsetAsync(h.toff[0], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.toff[1], 0, (size_t)(L.nptiles + 1) * 4, st));
+    INIT_CHECK(cudaMemsetAsync(h.coff[0], 0, (size_t)(L.nptiles + 1) * 4, st));
+    INIT_CHECK(cudaMemsetAsync(h.coff[1], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcnt, 0, (size_t)L.nptiles * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcur, 0, (size_t)L.nptiles * 4, st));
     INIT_CHECK(cudaMemsetAsync(s->d_counters, 0, 64, st));
@@ -602,13 +614,10 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     INIT_CHECK(cudaMemcpyAsync(s->d, &h, sizeof h, cudaMemcpyHostToDevice, st));
     // work lists of the single-simulation group
     {
-        std::vector<Work> pw(L.nptiles), yw(L.nytiles);
-        for (int i = 0; i < L.nptiles; ++i) pw[i] = {0, i};
+        std::vector<Work> yw(L.nytiles);
         for (int i = 0; i < L.nytiles; ++i) yw[i] = {0, i};
-        int zero = 0;
-        INIT_CHECK(cudaMemcpyAsync(s->d_pwork, pw.data(), pw.size() * sizeof(Work), cudaMemcpyHostToDevice, st));
         INIT_CHECK(cudaMemcpyAsync(s->d_ywork, yw.data(), yw.size() * sizeof(Work), cudaMemcpyHostToDevice, st));
-        INIT_CHECK(cudaMemcpyAsync(s->d_list, &zero, sizeof zero, cudaMemcpyHostToDevice, st));
+        INIT_CHECK(cudaMemsetAsync(s->d_gprefix, 0, 64, st));
         INIT_CHECK(cudaStreamSynchronize(st));
     }
     // seeded slab: linear into set 1, then sorted into set 0
@@ -635,11 +644,9 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     const int nsm = prop.multiProcessorCount;
     Group& g = s->grp;
     g.sims = s->d;
-    g.pwork = s->d_pwork;
-    g.npwork = L.nptiles;
+    g.gprefix = s->d_gprefix;
     g.ywork = s->d_ywork;
     g.nywork = L.nytiles;
-    g.simlist = s->d_list;
     g.nsims = 1;
     g.counters = s->d_counters;
     g.dim = cfg->dim;
@@ -654,9 +661,9 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     const int bp = std::max(1, prepare_push(cfg->dim, cfg->precision, L.push_smem));
     const int by = std::max(1, prepare_yee(cfg->dim, cfg->precision, L.yee_smem));
     const int bs = std::max(1, scatter_blocks_per_sm(cfg->dim, cfg->precision));
-    g.push_grid = std::max(1, std::min(L.nptiles, bp * nsm));
+    g.push_grid = std::max(1, std::min(L.max_chunks, bp * nsm));
     g.yee_grid = std::max(1, std::min(L.nytiles, by * nsm));
-    g.scatter_grid = std::max(1, std::min(L.nptiles, bs * nsm));
+    g.scatter_grid = std::max(1, std::min(L.max_chunks, bs * nsm));
     INIT_CHECK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     if ((r = capture_step(s)) != PIC_OK) return cleanup(r);
 #undef INIT_CHECK
@@ -682,6 +689,7 @@ pic_status pic_profile_step(pic_sim* s, int n_steps, void* stream, double* secon
     for (int i = 0; i < 5; ++i) seconds[i] = 0.0;
     pic_status r = PIC_OK;
     for (int k = 0; k < n_steps && r == PIC_OK; ++k) {
+        launch_prefix(s->grp, st);
         cudaEventRecord(ev[0], st);
         launch_push(s->grp, st);
         cudaEventRecord(ev[1], st);

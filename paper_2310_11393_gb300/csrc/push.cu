@@ -96,9 +96,36 @@ __device__ __forceinline__ void sm_add(double* a, double v)
     if (v != 0.0) atomicAdd(a, v);
 }
 
+// Global chunk k of a launch group -> simulation, tile and particle range.  Chunks are
+// numbered per simulation by the tile scan (coff / ctile) and across the group by gprefix.
+struct ChunkRef {
+    int sim, tile, p0, p1;
+};
+
+__device__ __forceinline__ ChunkRef chunk_of(const SimDev* __restrict__ sims, int nsims, const int* __restrict__ gprefix,
+                                             int k)
+{
+    int lo = 0, hi = nsims;   // largest s with gprefix[s] <= k
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (gprefix[m] <= k) lo = m; else hi = m;
+    }
+    const SimDev& S = sims[lo];
+    const int par = S.st->parity;
+    const int j = k - gprefix[lo];
+    const int t = S.ctile[par][j];
+    const int c = j - S.coff[par][t];
+    ChunkRef r;
+    r.sim = lo;
+    r.tile = t;
+    r.p0 = S.toff[par][t] + c * S.chunk;
+    r.p1 = min(r.p0 + S.chunk, S.toff[par][t + 1]);
+    return r;
+}
+
 template <int D, typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_push(const SimDev* __restrict__ sims, const Work* __restrict__ work,
-                                              int nwork, int* __restrict__ counter)
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_push(const SimDev* __restrict__ sims, int nsims,
+                                              const int* __restrict__ gprefix, int* __restrict__ counter)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -117,17 +144,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= nwork) break;
-        const Work wk = work[item];
-        const SimDev& S = sims[wk.sim];
+        if (item >= gprefix[nsims]) break;
+        const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
+        const SimDev& S = sims[ck.sim];
         DevState* st = S.st;
         const int par = st->parity;
-        const int p0 = S.toff[par][wk.tile], p1 = S.toff[par][wk.tile + 1];
-        if (p0 >= p1) continue;
+        const int p0 = ck.p0, p1 = ck.p1;
 
         int tc[3] = {0, 0, 0};
         {
-            int t = wk.tile;
+            int t = ck.tile;
             tc[0] = t % S.npt[0];
             t /= S.npt[0];
             if constexpr (D > 1) {
@@ -446,19 +472,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
     if (tid == 0) bulk_wait0();
 }
 
-// Exclusive scan of the destination counts of one simulation per block (1024 threads).
-__device__ void scan_counts(const SimDev& S, int outpar)
+// Block-wide exclusive scan of one int per thread (blockDim a multiple of 32, <= 1024).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp)
 {
-    __shared__ int s_warp[32];
-    const int n = S.nptiles;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int chunk = (n + nth - 1) / nth;
-    const int i0 = min(n, tid * chunk), i1 = min(n, i0 + chunk);
-    int local = 0;
-    for (int i = i0; i < i1; ++i) local += S.tcnt[i];
-    // block exclusive scan of `local`
-    const int lane = tid & 31, wid = tid >> 5;
-    int x = local;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, off);
@@ -467,7 +485,7 @@ __device__ void scan_counts(const SimDev& S, int outpar)
     if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        int w = lane < (nth >> 5) ? s_warp[lane] : 0;
+        int w = lane < nw ? s_warp[lane] : 0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, w, off);
@@ -476,27 +494,79 @@ __device__ void scan_counts(const SimDev& S, int outpar)
         s_warp[lane] = w;
     }
     __syncthreads();
-    int run = x - local + (wid > 0 ? s_warp[wid - 1] : 0);
-    int* out = S.toff[outpar];
+    const int r = x - v + (wid > 0 ? s_warp[wid - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan of the destination counts of one simulation (one block of 1024 threads):
+// tile offsets toff, chunk offsets coff (ceil(count / chunk) chunks per tile) and the
+// chunk -> tile map of buffer set `outpar`; clears the counts and cursors.
+__device__ void scan_counts(const SimDev& S, int outpar)
+{
+    __shared__ int s_warp[32];
+    const int n = S.nptiles;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int per = (n + nth - 1) / nth;
+    const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
+    int lp = 0, lc = 0;
     for (int i = i0; i < i1; ++i) {
-        out[i] = run;
-        run += S.tcnt[i];
+        const int c = S.tcnt[i];
+        lp += c;
+        lc += (c + S.chunk - 1) / S.chunk;
+    }
+    int rp = block_exclusive_scan(lp, s_warp);
+    int rc = block_exclusive_scan(lc, s_warp);
+    int* to = S.toff[outpar];
+    int* co = S.coff[outpar];
+    int* ct = S.ctile[outpar];
+    for (int i = i0; i < i1; ++i) {
+        const int c = S.tcnt[i];
+        const int nc = (c + S.chunk - 1) / S.chunk;
+        to[i] = rp;
+        co[i] = rc;
+        for (int k = 0; k < nc; ++k) ct[rc + k] = i;
+        rp += c;
+        rc += nc;
         S.tcnt[i] = 0;
         S.tcur[i] = 0;
     }
-    if (tid == nth - 1) out[n] = run;
+    if (tid == nth - 1) {
+        to[n] = rp;
+        co[n] = rc;
+    }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims, const int* __restrict__ list)
+__global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims)
 {
-    const SimDev& S = sims[list[blockIdx.x]];
+    const SimDev& S = sims[blockIdx.x];
     scan_counts(S, 1 - S.st->parity);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_one(const SimDev* __restrict__ sim)
 {
     scan_counts(*sim, 1 - sim->st->parity);
+}
+
+// First node of every step: number the chunks of the group's simulations and reset the
+// work counters.
+__global__ void __launch_bounds__(1024) k_prefix(const SimDev* __restrict__ sims, int nsims, int* __restrict__ gprefix,
+                                                 int* __restrict__ counters)
+{
+    __shared__ int s_warp[32];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int per = (nsims + nth - 1) / nth;
+    const int i0 = min(nsims, tid * per), i1 = min(nsims, i0 + per);
+    int l = 0;
+    for (int i = i0; i < i1; ++i) l += sims[i].coff[sims[i].st->parity][sims[i].nptiles];
+    int r = block_exclusive_scan(l, s_warp);
+    for (int i = i0; i < i1; ++i) {
+        gprefix[i] = r;
+        r += sims[i].coff[sims[i].st->parity][sims[i].nptiles];
+    }
+    if (tid == nth - 1) gprefix[nsims] = r;
+    if (tid < 4) counters[tid] = 0;
 }
 
 template <int D, typename R>
@@ -526,9 +596,12 @@ __device__ __forceinline__ int warp_reserve(int tile, int* cursors)
     return base + rank;
 }
 
+// Scatter of one chunk per work item: each warp reserves destination slots with one atomic
+// per distinct destination tile among its lanes (lanes going to the same tile write
+// consecutive slots).
 template <int D, typename R>
-__global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims, const Work* __restrict__ work,
-                                                 int nwork, int* __restrict__ counter)
+__global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims, int nsims,
+                                                 const int* __restrict__ gprefix, int* __restrict__ counter)
 {
     __shared__ int s_item;
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -537,15 +610,14 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= nwork) break;
-        const Work wk = work[item];
-        const SimDev& S = sims[wk.sim];
+        if (item >= gprefix[nsims]) break;
+        const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
+        const SimDev& S = sims[ck.sim];
         const int par = S.st->parity, np = 1 - par;
-        const int p0 = S.toff[par][wk.tile], p1 = S.toff[par][wk.tile + 1];
-        for (int base = p0; base < p1; base += nth) {
+        for (int base = ck.p0; base < ck.p1; base += nth) {
             const int p = base + tid;
             int t = -1;
-            if (p < p1) {
+            if (p < ck.p1) {
                 const unsigned cl = S.cell[par][p];
                 if (cl != DEAD) {
                     int c[3];
@@ -559,18 +631,16 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
     }
 }
 
-__global__ void k_step_end(const SimDev* __restrict__ sims, const int* __restrict__ list, int nsims,
-                           int* __restrict__ counters)
+__global__ void k_step_end(const SimDev* __restrict__ sims, int nsims)
 {
     for (int i = threadIdx.x; i < nsims; i += blockDim.x) {
-        const SimDev& S = sims[list[i]];
+        const SimDev& S = sims[i];
         DevState* st = S.st;
         const int np = 1 - st->parity;
         st->n_alive = S.toff[np][S.nptiles];
         st->parity = np;
         st->step += 1;
     }
-    if (threadIdx.x < 4) counters[threadIdx.x] = 0;
 }
 
 // ---- set-up ----------------------------------------------------------------------
@@ -646,12 +716,12 @@ __global__ void k_sort_linear(const SimDev* __restrict__ sim, long long n)
 template <int D, typename R>
 static void push_t(const Group& g, cudaStream_t s)
 {
-    k_push<D, R><<<g.push_grid, 256, g.push_smem, s>>>(g.sims, g.pwork, g.npwork, g.counters + 0);
+    k_push<D, R><<<g.push_grid, 256, g.push_smem, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 0);
 }
 template <int D, typename R>
 static void scatter_t(const Group& g, cudaStream_t s)
 {
-    k_scatter<D, R><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.pwork, g.npwork, g.counters + 1);
+    k_scatter<D, R><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
 }
 
 #define SFF_DISPATCH(dim, prec, FN, ...)                                 \
@@ -669,11 +739,9 @@ static void scatter_t(const Group& g, cudaStream_t s)
 
 void launch_push(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, push_t, g, s); }
 void launch_scatter(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, scatter_t, g, s); }
-void launch_scan(const Group& g, cudaStream_t s) { k_scan<<<g.nsims, 1024, 0, s>>>(g.sims, g.simlist); }
-void launch_step_end(const Group& g, cudaStream_t s)
-{
-    k_step_end<<<1, 256, 0, s>>>(g.sims, g.simlist, g.nsims, g.counters);
-}
+void launch_scan(const Group& g, cudaStream_t s) { k_scan<<<g.nsims, 1024, 0, s>>>(g.sims); }
+void launch_prefix(const Group& g, cudaStream_t s) { k_prefix<<<1, 1024, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters); }
+void launch_step_end(const Group& g, cudaStream_t s) { k_step_end<<<1, 256, 0, s>>>(g.sims, g.nsims); }
 void launch_scan_one(const SimDev* sim, int, int, cudaStream_t s) { k_scan_one<<<1, 1024, 0, s>>>(sim); }
 
 template <int D, typename R>

@@ -77,6 +77,10 @@ struct alignas(128) SimDev {
     void* wgt[2];
     unsigned* pid[2];
     int* toff[2];             // tile offsets [nptiles + 1] of each buffer set
+    int* coff[2];             // chunk offsets [nptiles + 1]: tile t owns chunks coff[t] .. coff[t+1]-1
+    int* ctile[2];            // chunk -> tile map [max_chunks]
+    int chunk;                // particles per chunk (the unit of work of push and scatter)
+    int max_chunks;
     int* tcnt;                // per-tile counts of the next step
     int* tcur;                // per-tile write cursors
     double* exits;            // [max_exits][EXIT_DOUBLES]

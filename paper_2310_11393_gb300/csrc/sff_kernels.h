@@ -17,14 +17,14 @@ __host__ __device__ constexpr int comp_eb(int parity) { return 6 * parity; }
 __host__ __device__ constexpr int comp_j(int parity) { return 12 + 3 * parity; }
 
 // One launch group: simulations of one dimension and precision advanced together.
+// Particles are processed in chunks of at most SimDev::chunk particles of one tile; the
+// chunks of all simulations of the group are numbered 0 .. gprefix[nsims)-1 each step.
 struct Group {
     const SimDev* sims;    // device array
-    const Work* pwork;     // particle tiles (sim, tile), device
-    int npwork;
+    int nsims;
+    int* gprefix;          // device [nsims + 1]: first global chunk of each simulation
     const Work* ywork;     // field-solver tiles, device
     int nywork;
-    const int* simlist;    // device: indices into sims
-    int nsims;
     int* counters;         // device: [0] push, [1] scatter, [2] field solver
     int dim, prec;
     size_t push_smem, yee_smem;
@@ -32,6 +32,7 @@ struct Group {
 };
 
 // per-step kernels (asynchronous)
+void launch_prefix(const Group& g, cudaStream_t s);
 void launch_push(const Group& g, cudaStream_t s);
 void launch_scan(const Group& g, cudaStream_t s);
 void launch_scatter(const Group& g, cudaStream_t s);

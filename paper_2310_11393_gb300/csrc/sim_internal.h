@@ -43,9 +43,8 @@ struct pic_sim {
     Arena arena;
     // single-simulation launch group
     Group grp{};
-    Work* d_pwork = nullptr;
     Work* d_ywork = nullptr;
-    int* d_list = nullptr;
+    int* d_gprefix = nullptr;    // chunk numbering of the single-simulation group
     int* d_counters = nullptr;
     double* d_acc = nullptr;     // 8 doubles
     unsigned long long* d_bits = nullptr;
