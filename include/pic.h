@@ -206,6 +206,21 @@ pic_status pic_diag(pic_sim* sim, int kind, void* host_out, size_t bytes, void* 
  * exits.  HOST output: double[n_e * n_a], angle fastest.  Synchronous. */
 pic_status pic_histogram(pic_sim* sim, int n_e, double e_max, int n_a, double* host_out, void* stream);
 
+/* Same weighted energy-angle histogram as pic_histogram, for callers that must not allocate
+ * device memory on the call path: for example a serving loop whose device memory is fully
+ * claimed by a framework's caching allocator, or a real-time loop that must not risk the
+ * device-wide synchronisation that cudaMalloc / cudaFree can cause.  It allocates nothing: the
+ * bins are accumulated in a file-scope device array of PIC_HIST_STATIC_MAX_BINS doubles
+ * (128 KiB) that every GPU which loads the library holds until the process exits.  The first
+ * call on a device looks the array up (cudaGetSymbolAddress) with that device current, so make
+ * that first call before any stream capture.  Every call clears the bins it uses and then
+ * leaves its result in the array; calls that overlap on the GPU (different streams or host
+ * threads) share the array and race, so serialise them.  n_e * n_a > PIC_HIST_STATIC_MAX_BINS
+ * is rejected with PIC_EINVAL.  HOST output double[n_e * n_a], angle fastest.  Synchronous.
+ * (No counterpart in the paper: this is an interface for constrained callers.) */
+#define PIC_HIST_STATIC_MAX_BINS 16384
+pic_status pic_histogram_static(pic_sim* sim, int n_e, double e_max, int n_a, double* host_out, void* stream);
+
 /* Evaluates the simulation's incident field with the device code path at n HOST points
  * pts[n][4] = (x, y, z, t) in grid coordinates; HOST out[n][6] = Ex Ey Ez Bx By Bz.
  * Synchronous.  Used to check the incident-field arithmetic point by point. */

@@ -6,9 +6,12 @@
 
 #include <algorithm>
 
+#include <mutex>
+
 #include "beam.cuh"
 #include "sff_common.cuh"
 #include "sff_kernels.h"
+#include "sim_internal.h"
 
 namespace sff {
 
@@ -317,3 +320,60 @@ void launch_eval_incident(const SimDev* sim, int dim, int prec, long long n, con
 }
 
 }  // namespace sff
+
+// ---- histogram with statically allocated bins (pic_histogram_static) ------------------------
+// The bins live in this file-scope array, so the call path allocates nothing.  Host code only
+// ever passes the array's device address, looked up once per device.
+static __device__ __align__(256) double g_hist_bins[PIC_HIST_STATIC_MAX_BINS];
+
+namespace {
+std::mutex g_hist_mu;
+double* g_hist_addr[64] = {nullptr};   // device address of g_hist_bins per device ordinal
+}  // namespace
+
+extern "C" pic_status pic_histogram_static(pic_sim* s, int n_e, double e_max, int n_a, double* host_out, void* stream)
+{
+    if (!s || !host_out || n_e <= 0 || n_a <= 0 || !(e_max > 0)) return PIC_EINVAL;
+    if ((long long)n_e * n_a > PIC_HIST_STATIC_MAX_BINS) {
+        s->err = "pic_histogram_static: n_e * n_a exceeds PIC_HIST_STATIC_MAX_BINS (16384)";
+        return PIC_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        s->err = "pic_histogram_static: no current CUDA device";
+        return PIC_ENODEV;
+    }
+    double* bins = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_hist_mu);
+        if (!g_hist_addr[dev]) {
+            // set-up, once per device, with that device current
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_hist_bins);
+            if (e != cudaSuccess) {
+                s->err = std::string("pic_histogram_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+                return PIC_ECUDA;
+            }
+            g_hist_addr[dev] = static_cast<double*>(p);
+        }
+        bins = g_hist_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    sff::DevState ds;
+    cudaError_t e = cudaMemcpyAsync(&ds, s->h.st, sizeof(sff::DevState), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const size_t nb = (size_t)n_e * n_a;
+    if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, nb * sizeof(double), st);
+    if (e == cudaSuccess) {
+        sff::launch_histogram(s->d, s->cfg.dim, s->cfg.precision, ds.n_alive,
+                              std::min<long long>(ds.n_exits, s->h.max_exits), n_e, e_max, n_a, bins, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, bins, nb * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        s->err = std::string("pic_histogram_static: ") + cudaGetErrorString(e);
+        return PIC_ECUDA;
+    }
+    return PIC_OK;
+}

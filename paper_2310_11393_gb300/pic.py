@@ -108,6 +108,8 @@ def load():
     L.pic_diag.argtypes = [P, c_int, P, c_size_t, P]
     L.pic_histogram.restype = c_int
     L.pic_histogram.argtypes = [P, c_int, c_double, c_int, DP, P]
+    L.pic_histogram_static.restype = c_int
+    L.pic_histogram_static.argtypes = [P, c_int, c_double, c_int, DP, P]
     L.pic_eval_incident.restype = c_int
     L.pic_eval_incident.argtypes = [P, c_int64, DP, DP, P]
     L.pic_batch_step.restype = c_int
@@ -207,6 +209,15 @@ def pic_diag(sim, kind: int, out: np.ndarray, stream=0):
 def pic_histogram(sim, n_e: int, e_max: float, n_a: int, stream=0) -> np.ndarray:
     out = np.zeros((n_e, n_a))
     check(load().pic_histogram(sim, n_e, e_max, n_a, _dp(out), c_void_p(stream)), sim)
+    return out
+
+
+PIC_HIST_STATIC_MAX_BINS = 16384
+
+
+def pic_histogram_static(sim, n_e: int, e_max: float, n_a: int, stream=0) -> np.ndarray:
+    out = np.zeros((n_e, n_a))
+    check(load().pic_histogram_static(sim, n_e, e_max, n_a, _dp(out), c_void_p(stream)), sim)
     return out
 
 
