@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (default: the workload's full run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d"])
+    ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "batch", "serve"])
+    ap.add_argument("--sims", type=int, default=256, help="batch: number of simulations")
+    ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (1/s)")
     ap.add_argument("--profile-steps", type=int, default=0, help="steps timed kernel by kernel (default: --steps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -309,8 +312,132 @@ def run_reference(args, rank, world):
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batch(args):
+    """Batched 2D workload: `--sims` independent runs of uneven size (LP/RP mix).  The same
+    K steps of every simulation are timed (a) one simulation after another, each through its
+    own step graph, and (b) all together through pic_batch_step (one persistent launch per
+    phase over every simulation's work, one graph)."""
+    import torch
+
+    from paper_2310_11393_gb300 import _build, pic
+
+    _build.build()
+    torch.cuda.set_device(0)
+    ws = synth.c4_batch(args.sims)
+    stream = torch.cuda.current_stream().cuda_stream
+    K = args.steps
+    out = {}
+    for mode in ("plain", "batched"):
+        sims = [pic.Simulation(pic.config_from(w), stream=stream) for w in ws]
+        n0 = sum(s.info().n_alive for s in sims)
+        # warm-up (graphs, attributes, batch graph capture)
+        if mode == "plain":
+            for s in sims:
+                s.step(args.warmup)
+        else:
+            pic.pic_batch_step([s.h for s in sims], args.warmup, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if mode == "plain":
+            for s in sims:
+                s.step(K)
+        else:
+            pic.pic_batch_step([s.h for s in sims], K, stream)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) * 1e-3
+        n1 = sum(s.info().n_alive for s in sims)
+        out[mode] = {"pushes_per_s": 0.5 * (n0 + n1) * K / secs, "seconds": secs}
+        for s in sims:
+            s.close()
+    cells = sum(w.n_cells for w in ws)
+    ratio = out["batched"]["pushes_per_s"] / out["plain"]["pushes_per_s"]
+    return {"metric": "batched particle-pushes/s (256 uneven 2D runs)", "value": out["batched"]["pushes_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch2d_{len(ws)}", "sims": len(ws), "cells": cells,
+                       "particles": int(sum(w.n_particles for w in ws)),
+                       "sample": f"steps {args.warmup}..{args.warmup + K} of each 500-step run"},
+            "plain": out["plain"], "batched": out["batched"], "batched_over_plain": ratio}
+
+
+def run_serve(args):
+    """Served parameter scan: a Poisson stream of 2D and 3D RP runs submitted to pic_serve at
+    the given rate; time-to-result p50/p99 and aggregate pushes/s, next to the same requests
+    run back to back on one stream (each started when the previous one finished)."""
+    import torch
+
+    from paper_2310_11393_gb300 import _build, pic
+
+    _build.build()
+    torch.cuda.set_device(0)
+    reqs = synth.c5_requests(args.requests, rate_hz=args.rate, max_2d=512, max_3d=160, steps_range=(500, 2000))
+    # plain: back to back, arrival times honoured (a request waits for the previous one)
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    lat_plain = []
+    pushes = 0
+    clock = 0.0
+    for (ta, w) in reqs:
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        s = pic.Simulation(pic.config_from(w), stream=stream)
+        n = s.info().n_alive
+        s.step(w.steps)
+        s.energies()
+        s.close()
+        pushes += n * w.steps
+        lat_plain.append(time.perf_counter() - t0 - ta)
+    plain_secs = time.perf_counter() - t0
+    srv = pic.pic_serve_open(quantum=50)
+    t0 = pic.pic_serve_clock(srv)
+    w0 = time.perf_counter()
+    tickets = []
+    for (ta, w) in reqs:
+        now = time.perf_counter() - w0
+        if now < ta:
+            time.sleep(ta - now)
+        tickets.append(pic.pic_serve_submit(srv, pic.config_from(w), w.steps))
+    res = {}
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t in res:
+                continue
+            st, r = pic.pic_serve_poll(srv, t)
+            if st != pic.PIC_EBUSY:
+                res[t] = (st, r)
+        time.sleep(0.005)
+    served_secs = pic.pic_serve_clock(srv) - t0
+    pic.pic_serve_close(srv)
+    lat = [r.finish_time - r.submit_time for (st, r) in res.values()]
+    ok = sum(1 for (st, r) in res.values() if st == pic.PIC_OK)
+    spushes = sum(r.pushes for (st, r) in res.values())
+    check = {"steps_requested": int(sum(w.steps for _, w in reqs)),
+             "steps_done": int(sum(r.steps_done for (st, r) in res.values())),
+             "pushes_reported": int(spushes), "pushes_plain": int(pushes)}
+    q = lambda v, p: float(np.percentile(v, p))
+    return {"metric": "served time-to-result p50/p99 and pushes/s", "value": spushes / served_secs, "unit": UNIT,
+            "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served_scan", "requests": len(reqs), "rate_hz": args.rate,
+                       "sizes": "2D 256-512^2 or 3D 128-160^3, RP, 500-2000 steps"},
+            "served": {"p50_s": q(lat, 50), "p99_s": q(lat, 99), "pushes_per_s": spushes / served_secs,
+                       "completed": ok, "makespan_s": served_secs},
+            "plain": {"p50_s": q(lat_plain, 50), "p99_s": q(lat_plain, 99), "pushes_per_s": pushes / plain_secs,
+                      "makespan_s": plain_secs}, "check": check}
+
+
 def main():
     args = parse()
+    if args.workload == "batch":
+        args.steps = args.steps if args.steps > 0 else 100
+        print(json.dumps(run_batch(args)))
+        return
+    if args.workload == "serve":
+        print(json.dumps(run_serve(args)))
+        return
     if args.steps <= 0:
         args.steps = workload(args.workload).steps
     world = int(os.environ.get("WORLD_SIZE", "1"))

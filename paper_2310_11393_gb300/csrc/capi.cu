@@ -203,6 +203,7 @@ pic_status validate(const pic_config* c, pic_sim* s)
 void choose_tiles(const pic_config* c, int pt[3], int yt[3])
 {
     const bool fp64 = c->precision == PIC_FP64;
+    // field-solver tiles are fixed per dimension: k_yee is compiled for exactly these shapes
     if (c->dim == 1) {
         pt[0] = 32; yt[0] = 128;
     } else if (c->dim == 2) {
@@ -569,6 +570,9 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
     h.cap = L.cap;
     h.bcf = make_beam_consts<float>(h);
     h.bcd = make_beam_consts<double>(h);
+    h.ycf = {(float)(prm.dt / cfg->dx), (float)(0.5 * prm.dt / cfg->dx), (float)prm.dt,
+             (float)((prm.dt - cfg->dx) / (prm.dt + cfg->dx))};
+    h.ycd = {prm.dt / cfg->dx, 0.5 * prm.dt / cfg->dx, prm.dt, (prm.dt - cfg->dx) / (prm.dt + cfg->dx)};
     // tensor maps (every box extent must stay within TMA's 256 elements per dimension)
     for (int d = 0; d < 3; ++d)
         if (L.pb[d] > 256 || L.yb[d] > 256) {

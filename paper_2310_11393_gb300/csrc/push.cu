@@ -198,7 +198,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
         const R hq = R(-0.5 * S.dt);                // q dt / 2
         const int hx[3] = {4, 2, 2};                // box halo below the tile per axis
 
-        for (int p = p0 + tid; p < p1; p += nth) {
+        // Rounds of 256 particles; within a round lane l of warp w takes particle 8 l + w, so
+        // the 32 lanes of a warp are spread over the round (and over cells: 8 particles per
+        // cell sit next to each other after the sort) rather than walking consecutive, often
+        // same-cell, particles: fewer same-address shared-memory atomics in the deposit.
+        const int q = (tid & 31) * 8 + (tid >> 5);
+        for (int rb = p0; rb < p1; rb += nth) {
+            const int p = rb + q;
+            if (p >= p1) continue;
             const unsigned cl = S.cell[par][p];
             int c[3];
             decode_cell<D>(S, cl, c);

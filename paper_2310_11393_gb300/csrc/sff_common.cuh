@@ -40,6 +40,15 @@ struct BeamC {
     R eu[3], bu[3];
 };
 
+// Field-solver constants in the working precision R, computed on the host at set-up.
+template <typename R>
+struct YeeC {
+    R cdt;   // dt/dx
+    R hc;    // dt/(2 dx)
+    R dt;
+    R km;    // (dt - dx)/(dt + dx), first-order Mur
+};
+
 // Everything a kernel needs to know about one simulation.  Lives in device memory
 // (an array of these serves a batch); tensor maps must stay 64-byte aligned.
 struct alignas(128) SimDev {
@@ -91,7 +100,16 @@ struct alignas(128) SimDev {
     double* scratch;          // diagnostics scratch: charge density, same layout
     BeamC<float> bcf;         // incident-field constants for the FP32 kernels
     BeamC<double> bcd;        // ... and the FP64 kernels
+    YeeC<float> ycf;          // field-solver constants, FP32 and FP64
+    YeeC<double> ycd;
 };
+
+template <typename R>
+__device__ __forceinline__ const YeeC<R>& yee_of(const SimDev& S)
+{
+    if constexpr (sizeof(R) == 4) return S.ycf;
+    else return S.ycd;
+}
 
 template <typename R>
 __device__ __forceinline__ const BeamC<R>& beam_of(const SimDev& S)

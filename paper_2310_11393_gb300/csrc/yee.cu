@@ -1,8 +1,8 @@
 // Field solver of the scattered field (Eqs. MAmper, MFaraday; Yee stagger), sm_103a.
 //
-// One work item = one tile of the grid.  The tile's box (x: 4 points of halo below and
-// above, y/z: 2) of E, B at step n (buffer set p) and of J^{n+1/2} (J_p) arrives by two
-// TMA loads.  In shared memory:
+// One work item = one tile of TX x TY x TZ points (compile-time shape).  The tile's box
+// (x: 4 points of halo on each side, y/z: 2) of E, B at step n (buffer set p) and of
+// J^{n+1/2} (J_p) arrives by two TMA loads.  In shared memory:
 //   A. B^{n+1/2} = B^n - (dt/2) curl E^n             (forward differences, in place)
 //   B. E^{n+1}   = E^n + dt (curl B^{n+1/2} - J)      (backward differences, into the J slots)
 //      except on faces, where
@@ -10,6 +10,7 @@
 //      the lowest face axis of the point, points on fewer faces first;
 //   D. B^{n+1}   = B^{n+1/2} - (dt/2) curl E^{n+1}    on the tile, points a component does
 //      not have (outside [0, n] / [0, n-1]) forced to zero.
+// Tiles whose box touches no face (most of them) skip the face tests and phase C.
 // The tile of E^{n+1}, B^{n+1} leaves by one TMA store into buffer set 1-p, and J_{1-p}
 // (the next step's deposit target) is cleared on the tile.  No CTA writes what another
 // reads in the same launch.
@@ -46,20 +47,38 @@ __device__ __forceinline__ bool has_point(const SimDev& S, int comp, const int g
     return true;
 }
 
-template <int D, typename R>
+template <int D, typename R, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, const Work* __restrict__ work,
                                              int nwork, int* __restrict__ counter)
 {
+    constexpr int HX = 4, HY = D > 1 ? 2 : 0, HZ = D > 2 ? 2 : 0;
+    constexpr int EX = TX + 2 * HX, EY = TY + 2 * HY, EZ = TZ + 2 * HZ;
+    constexpr int SY = EX, SZ = EX * EY, BV = EX * EY * EZ, TV = TX * TY * TZ;
+    constexpr size_t JOFF = round128(6 * BV * sizeof(R));
+    constexpr size_t OOFF = round128(JOFF + 3 * BV * sizeof(R));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x;
+    constexpr int NT = 256;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     unsigned phase = 0;
+    R* In = reinterpret_cast<R*>(smem_raw);            // [6][EZ][EY][EX]: Ex Ey Ez Bx By Bz
+    R* Jn = reinterpret_cast<R*>(smem_raw + JOFF);     // [3][EZ][EY][EX]: J, then E^{n+1}
+    R* Out = reinterpret_cast<R*>(smem_raw + OOFF);    // [6][TZ][TY][TX]
+    R* Ex = In;
+    R* Ey = In + BV;
+    R* Ez = In + 2 * BV;
+    R* Bx = In + 3 * BV;
+    R* By = In + 4 * BV;
+    R* Bz = In + 5 * BV;
+    R* Nx = Jn;
+    R* Ny = Jn + BV;
+    R* Nz = Jn + 2 * BV;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -70,7 +89,6 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
         const SimDev& S = sims[wk.sim];
         DevState* st = S.st;
         const int par = st->parity;
-
         int tc[3] = {0, 0, 0};
         {
             int t = wk.tile;
@@ -82,27 +100,27 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
             }
             if constexpr (D > 2) tc[2] = t;
         }
-        const int T[3] = {S.yt[0], D > 1 ? S.yt[1] : 1, D > 2 ? S.yt[2] : 1};
-        const int lo[3] = {tc[0] * T[0], tc[1] * T[1], tc[2] * T[2]};
-        const int hx[3] = {4, D > 1 ? 2 : 0, D > 2 ? 2 : 0};
-        const int e[3] = {S.yb[0], D > 1 ? S.yb[1] : 1, D > 2 ? S.yb[2] : 1};
-        const int sx = 1, sy = e[0], sz = e[0] * e[1];
-        const int bvol = e[0] * e[1] * e[2];
-        const int tvol = T[0] * T[1] * T[2];
-        const size_t joff = round128(6 * bvol * sizeof(R));
-        const size_t ooff = round128(joff + 3 * bvol * sizeof(R));
-        R* In = reinterpret_cast<R*>(smem_raw);                 // [6][e_z][e_y][e_x]: Ex Ey Ez Bx By Bz
-        R* Jn = reinterpret_cast<R*>(smem_raw + joff);          // [3][e_z][e_y][e_x]: J, then E^{n+1}
-        R* Out = reinterpret_cast<R*>(smem_raw + ooff);         // [6][T_z][T_y][T_x]
-        const int org[3] = {lo[0] - hx[0] + G, D > 1 ? lo[1] - hx[1] + G : 0, D > 2 ? lo[2] - hx[2] + G : 0};
+        const int lo[3] = {tc[0] * TX, tc[1] * TY, tc[2] * TZ};
+        const int org[3] = {lo[0] - HX + G, D > 1 ? lo[1] - HY + G : 0, D > 2 ? lo[2] - HZ + G : 0};
         if (tid == 0) {
             tensormap_acquire(&S.tm_yin);
             tensormap_acquire(&S.tm_yj);
             tensormap_acquire(&S.tm_yout);
-            mbar_arrive_expect_tx(&bar, (unsigned)(9 * bvol * sizeof(R)));
+            mbar_arrive_expect_tx(&bar, (unsigned)(9 * BV * sizeof(R)));
             tma_load_box<D>(In, &S.tm_yin, org, comp_eb(par), &bar);
             tma_load_box<D>(Jn, &S.tm_yj, org, comp_j(par), &bar);
         }
+        // the box reaches global points lo - h .. lo - h + E - 1; phases use 1 .. E - 2
+        bool interior = true;
+        {
+            const int h[3] = {HX, HY, HZ};
+            const int e[3] = {EX, EY, EZ};
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                if (lo[d] - h[d] + 1 <= 0 || lo[d] - h[d] + e[d] - 2 >= S.n[d]) interior = false;
+        }
+        const YeeC<R>& yc = yee_of<R>(S);
+        const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
         const bool ok = mbar_wait_bounded(&bar, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
@@ -113,98 +131,102 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
             }
             return;
         }
-        R* Ex = In;
-        R* Ey = In + bvol;
-        R* Ez = In + 2 * bvol;
-        R* Bx = In + 3 * bvol;
-        R* By = In + 4 * bvol;
-        R* Bz = In + 5 * bvol;
-        R* Nx = Jn;              // J on entry, E^{n+1} after phase B
-        R* Ny = Jn + bvol;
-        R* Nz = Jn + 2 * bvol;
-        const R cdt = R(S.dt * S.inv_dx);
-        const R hc = R(0.5) * cdt;
-        const R dt = R(S.dt);
-        const R km = R((S.dt - S.dx) / (S.dt + S.dx));
 
-        // A. B^{n+1/2} in place
-        for (int i = tid; i < bvol; i += nth) {
-            const int lx = i % e[0], ly = (i / e[0]) % e[1], lz = i / sz;
-            if (lx >= e[0] - 1) continue;
-            if (D > 1 && ly >= e[1] - 1) continue;
-            if (D > 2 && lz >= e[2] - 1) continue;
-            const R dEz_dy = D > 1 ? Ez[i + sy] - Ez[i] : R(0);
-            const R dEx_dy = D > 1 ? Ex[i + sy] - Ex[i] : R(0);
-            const R dEy_dz = D > 2 ? Ey[i + sz] - Ey[i] : R(0);
-            const R dEx_dz = D > 2 ? Ex[i + sz] - Ex[i] : R(0);
-            const R dEz_dx = Ez[i + sx] - Ez[i];
-            const R dEy_dx = Ey[i + sx] - Ey[i];
+        // A. B^{n+1/2} in place, points 0 .. E-2 on every resolved axis
+        for (int i = tid; i < BV; i += NT) {
+            const int lx = i % EX, ly = (i / EX) % EY, lz = i / SZ;
+            if (lx >= EX - 1) continue;
+            if (D > 1 && ly >= EY - 1) continue;
+            if (D > 2 && lz >= EZ - 1) continue;
+            const R dEz_dy = D > 1 ? Ez[i + SY] - Ez[i] : R(0);
+            const R dEx_dy = D > 1 ? Ex[i + SY] - Ex[i] : R(0);
+            const R dEy_dz = D > 2 ? Ey[i + SZ] - Ey[i] : R(0);
+            const R dEx_dz = D > 2 ? Ex[i + SZ] - Ex[i] : R(0);
+            const R dEz_dx = Ez[i + 1] - Ez[i];
+            const R dEy_dx = Ey[i + 1] - Ey[i];
             Bx[i] -= hc * (dEz_dy - dEy_dz);
             By[i] -= hc * (dEx_dz - dEz_dx);
             Bz[i] -= hc * (dEy_dx - dEx_dy);
         }
         __syncthreads();
 
-        // B. E^{n+1} into the J slots at points 1..e-2 on every resolved axis, off the faces
-        for (int i = tid; i < bvol; i += nth) {
-            const int l[3] = {i % e[0], (i / e[0]) % e[1], i / sz};
-            if (l[0] < 1 || l[0] >= e[0] - 1) continue;
-            if (D > 1 && (l[1] < 1 || l[1] >= e[1] - 1)) continue;
-            if (D > 2 && (l[2] < 1 || l[2] >= e[2] - 1)) continue;
-            const int g[3] = {lo[0] - hx[0] + l[0], lo[1] - hx[1] + l[1], lo[2] - hx[2] + l[2]};
-            const R dBz_dy = D > 1 ? Bz[i] - Bz[i - sy] : R(0);
-            const R dBx_dy = D > 1 ? Bx[i] - Bx[i - sy] : R(0);
-            const R dBy_dz = D > 2 ? By[i] - By[i - sz] : R(0);
-            const R dBx_dz = D > 2 ? Bx[i] - Bx[i - sz] : R(0);
-            const R dBz_dx = Bz[i] - Bz[i - sx];
-            const R dBy_dx = By[i] - By[i - sx];
-            if (!face_axes<D>(S, 0, g)) Nx[i] = Ex[i] + cdt * (dBz_dy - dBy_dz) - dt * Nx[i];
-            if (!face_axes<D>(S, 1, g)) Ny[i] = Ey[i] + cdt * (dBx_dz - dBz_dx) - dt * Ny[i];
-            if (!face_axes<D>(S, 2, g)) Nz[i] = Ez[i] + cdt * (dBy_dx - dBx_dy) - dt * Nz[i];
+        // B. E^{n+1} into the J slots at points 1 .. E-2 on every resolved axis, off the faces
+        for (int i = tid; i < BV; i += NT) {
+            const int lx = i % EX, ly = (i / EX) % EY, lz = i / SZ;
+            if (lx < 1 || lx >= EX - 1) continue;
+            if (D > 1 && (ly < 1 || ly >= EY - 1)) continue;
+            if (D > 2 && (lz < 1 || lz >= EZ - 1)) continue;
+            const R dBz_dy = D > 1 ? Bz[i] - Bz[i - SY] : R(0);
+            const R dBx_dy = D > 1 ? Bx[i] - Bx[i - SY] : R(0);
+            const R dBy_dz = D > 2 ? By[i] - By[i - SZ] : R(0);
+            const R dBx_dz = D > 2 ? Bx[i] - Bx[i - SZ] : R(0);
+            const R dBz_dx = Bz[i] - Bz[i - 1];
+            const R dBy_dx = By[i] - By[i - 1];
+            const R ex = Ex[i] + cdt * (dBz_dy - dBy_dz) - dt * Nx[i];
+            const R ey = Ey[i] + cdt * (dBx_dz - dBz_dx) - dt * Ny[i];
+            const R ez = Ez[i] + cdt * (dBy_dx - dBx_dy) - dt * Nz[i];
+            if (interior) {
+                Nx[i] = ex;
+                Ny[i] = ey;
+                Nz[i] = ez;
+            } else {
+                const int g[3] = {lo[0] - HX + lx, lo[1] - HY + ly, lo[2] - HZ + lz};
+                if (!face_axes<D>(S, 0, g)) Nx[i] = ex;
+                if (!face_axes<D>(S, 1, g)) Ny[i] = ey;
+                if (!face_axes<D>(S, 2, g)) Nz[i] = ez;
+            }
         }
         __syncthreads();
 
-        // C. Mur faces, points on one face first, then edges, then corners
-        const int es[3] = {sx, sy, sz};
-        for (int pass = 1; pass <= D; ++pass) {
-            for (int i = tid; i < bvol; i += nth) {
-                const int l[3] = {i % e[0], (i / e[0]) % e[1], i / sz};
-                if (l[0] < 1 || l[0] >= e[0] - 1) continue;
-                if (D > 1 && (l[1] < 1 || l[1] >= e[1] - 1)) continue;
-                if (D > 2 && (l[2] < 1 || l[2] >= e[2] - 1)) continue;
-                const int g[3] = {lo[0] - hx[0] + l[0], lo[1] - hx[1] + l[1], lo[2] - hx[2] + l[2]};
+        // C. Mur faces (tiles touching a face only): one face first, then edges, then corners
+        if (!interior) {
+            const int es[3] = {1, SY, SZ};
+            const int e[3] = {EX, EY, EZ};
+            for (int pass = 1; pass <= D; ++pass) {
+                for (int i = tid; i < BV; i += NT) {
+                    const int l[3] = {i % EX, (i / EX) % EY, i / SZ};
+                    if (l[0] < 1 || l[0] >= EX - 1) continue;
+                    if (D > 1 && (l[1] < 1 || l[1] >= EY - 1)) continue;
+                    if (D > 2 && (l[2] < 1 || l[2] >= EZ - 1)) continue;
+                    const int g[3] = {lo[0] - HX + l[0], lo[1] - HY + l[1], lo[2] - HZ + l[2]};
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int m = face_axes<D>(S, c, g);
-                    if (!m || __popc(m) != pass) continue;
-                    const int a = __ffs(m) - 1;
-                    const int dir = (g[a] == 0) ? 1 : -1;
-                    const int ln = l[a] + dir;
-                    if (ln < 1 || ln >= e[a] - 1) continue;
-                    const int nb = i + dir * es[a];
-                    const R* Eo = In + c * bvol;
-                    R* En = Jn + c * bvol;
-                    En[i] = Eo[nb] + km * (En[nb] - Eo[i]);
+                    for (int c = 0; c < 3; ++c) {
+                        const int m = face_axes<D>(S, c, g);
+                        if (!m || __popc(m) != pass) continue;
+                        const int a = __ffs(m) - 1;
+                        const int dir = (g[a] == 0) ? 1 : -1;
+                        const int ln = l[a] + dir;
+                        if (ln < 1 || ln >= e[a] - 1) continue;
+                        const int nb = i + dir * es[a];
+                        const R* Eo = In + c * BV;
+                        R* En = Jn + c * BV;
+                        En[i] = Eo[nb] + km * (En[nb] - Eo[i]);
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
 
         // D. E^{n+1}, B^{n+1} on the tile
-        for (int k = tid; k < tvol; k += nth) {
-            const int t0 = k % T[0], t1 = (k / T[0]) % T[1], t2 = k / (T[0] * T[1]);
-            const int i = (t0 + hx[0]) + (t1 + hx[1]) * sy + (t2 + hx[2]) * sz;
-            const int g[3] = {lo[0] + t0, lo[1] + t1, lo[2] + t2};
-            const R dNz_dy = D > 1 ? Nz[i + sy] - Nz[i] : R(0);
-            const R dNx_dy = D > 1 ? Nx[i + sy] - Nx[i] : R(0);
-            const R dNy_dz = D > 2 ? Ny[i + sz] - Ny[i] : R(0);
-            const R dNx_dz = D > 2 ? Nx[i + sz] - Nx[i] : R(0);
-            const R dNz_dx = Nz[i + sx] - Nz[i];
-            const R dNy_dx = Ny[i + sx] - Ny[i];
+        for (int k = tid; k < TV; k += NT) {
+            const int t0 = k % TX, t1 = (k / TX) % TY, t2 = k / (TX * TY);
+            const int i = (t0 + HX) + (t1 + HY) * SY + (t2 + HZ) * SZ;
+            const R dNz_dy = D > 1 ? Nz[i + SY] - Nz[i] : R(0);
+            const R dNx_dy = D > 1 ? Nx[i + SY] - Nx[i] : R(0);
+            const R dNy_dz = D > 2 ? Ny[i + SZ] - Ny[i] : R(0);
+            const R dNx_dz = D > 2 ? Nx[i + SZ] - Nx[i] : R(0);
+            const R dNz_dx = Nz[i + 1] - Nz[i];
+            const R dNy_dx = Ny[i + 1] - Ny[i];
             const R v[6] = {Nx[i], Ny[i], Nz[i], Bx[i] - hc * (dNz_dy - dNy_dz), By[i] - hc * (dNx_dz - dNz_dx),
                             Bz[i] - hc * (dNy_dx - dNx_dy)};
+            if (interior) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) Out[c * tvol + k] = has_point<D>(S, c, g) ? v[c] : R(0);
+                for (int c = 0; c < 6; ++c) Out[c * TV + k] = v[c];
+            } else {
+                const int g[3] = {lo[0] + t0, lo[1] + t1, lo[2] + t2};
+#pragma unroll
+                for (int c = 0; c < 6; ++c) Out[c * TV + k] = has_point<D>(S, c, g) ? v[c] : R(0);
+            }
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -217,9 +239,9 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
         {
             R* Fg = reinterpret_cast<R*>(S.F);
             const long long jb = (long long)comp_j(1 - par) * S.sc;
-            for (int k = tid; k < 3 * tvol; k += nth) {
-                const int c = k / tvol, r = k - c * tvol;
-                const int t0 = r % T[0], t1 = (r / T[0]) % T[1], t2 = r / (T[0] * T[1]);
+            for (int k = tid; k < 3 * TV; k += NT) {
+                const int c = k / TV, r = k - c * TV;
+                const int t0 = r % TX, t1 = (r / TX) % TY, t2 = r / (TX * TY);
                 Fg[jb + c * S.sc + (long long)(D > 2 ? lo[2] + t2 + G : 0) * S.sz +
                    (long long)(D > 1 ? lo[1] + t1 + G : 0) * S.sy + (lo[0] + t0 + G)] = R(0);
             }
@@ -230,17 +252,35 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
     if (tid == 0) bulk_wait0();
 }
 
+// field-solver tiles per dimension (must match the host's tile choice)
+template <int D>
+struct YeeTile;
+template <>
+struct YeeTile<1> {
+    static constexpr int X = 128, Y = 1, Z = 1;
+};
+template <>
+struct YeeTile<2> {
+    static constexpr int X = 32, Y = 16, Z = 1;
+};
+template <>
+struct YeeTile<3> {
+    static constexpr int X = 8, Y = 8, Z = 8;
+};
+
 template <int D, typename R>
 static void yee_t(const Group& g, cudaStream_t s)
 {
-    k_yee<D, R><<<g.yee_grid, 256, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
+        <<<g.yee_grid, 256, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
 }
 
 template <int D, typename R>
 static void attr_yee(size_t smem, int* out)
 {
-    cudaFuncSetAttribute(k_yee<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_yee<D, R>, 256, smem);
+    auto k = k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, 256, smem);
 }
 
 #define SFF_DISPATCH2(dim, prec, FN, ...)                       \
