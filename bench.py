@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "batch", "serve"])
+    ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
+    ap.add_argument("--autotune", type=int, default=4,
+                    help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
     ap.add_argument("--sims", type=int, default=256, help="batch: number of simulations")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (1/s)")
@@ -50,8 +53,12 @@ def parse():
     return ap.parse_args()
 
 
+SCALE = 1
+
+
 def workload(name):
-    return {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp}[name]()
+    w = {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp}[name]()
+    return w if SCALE == 1 else synth.scaled(w, SCALE)
 
 
 def peaks():
@@ -154,6 +161,16 @@ def run_ours(args, rank, world, local_rank):
     cfg = pic.config_from(w)
     stream = torch.cuda.current_stream(dev).cuda_stream
     alloc = pic.torch_allocator(local_rank)
+    # tile and work-item size: measured by the autotuner (untimed set-up)
+    tune = {"trial_steps": args.autotune}
+    if args.autotune > 0:
+        t0 = time.perf_counter()
+        tune["ms_per_step_at_focus"] = round(pic.pic_autotune(cfg, args.autotune, stream), 4)
+        tune["seconds"] = round(time.perf_counter() - t0, 2)
+    prm = pic.pic_derive_params(cfg)
+    tune["push_tile"] = list(prm.tile)[: w.dim]
+    tune["chunk"] = prm.chunk
+    tune["field_solver_tile"] = list(prm.yee_tile)[: w.dim]
     # warm-up: W steps on a throw-away instance (clocks, caches, graph, launch attributes)
     warm = pic.Simulation(cfg, allocator=alloc, stream=stream)
     warm.step(args.warmup)
@@ -235,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, w, pic, torch, dev, stream, alloc)
+        e2e = run_e2e(args, w, cfg, pic, torch, dev, stream, alloc)
     out = {"metric": METRIC, "value": tot_pushes / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if es == 4 else "f64", "data": "synthetic",
@@ -244,16 +261,15 @@ def run_ours(args, rank, world, local_rank):
                       "precision": "fp32 body, fp64 phase" if es == 4 else "fp64",
                       "cell_updates_per_s": cells * args.steps * world / t_max,
                       "l2": "inputs larger than L2 (device state %.2f GB > 129 MB)" % (info.params.device_bytes / 1e9),
-                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "tiles": tune},
            "roofline": roof, "clocks": clk, "gpu_launches": 5 * args.steps, "e2e": e2e}
     return out
 
 
-def run_e2e(args, w, pic, torch, dev, stream, alloc):
+def run_e2e(args, w, cfg, pic, torch, dev, stream, alloc):
     """Through the C-ABI with HOST buffers: the initial particle state goes host -> device, the
     steps run, the energies and every particle's state come back device -> host."""
     x, u, wt, ids = synth.slab_particles(w)
-    cfg = pic.config_from(w)
     sim = pic.Simulation(cfg, allocator=alloc, stream=stream)
     n = len(ids)
     es = 4 if w.precision == synth.FP32 else 8
@@ -327,8 +343,16 @@ def run_batch(args):
     stream = torch.cuda.current_stream().cuda_stream
     K = args.steps
     out = {}
+    c0 = pic.config_from(ws[0])
+    if args.autotune > 0:
+        pic.pic_autotune(c0, args.autotune, stream)
+    tile, chunk = list(c0.tile), c0.chunk
+
+    def cfg_of(w):
+        return pic.config_from(w, tile=tile if args.autotune > 0 else None, chunk=chunk if args.autotune > 0 else 0)
+
     for mode in ("plain", "batched"):
-        sims = [pic.Simulation(pic.config_from(w), stream=stream) for w in ws]
+        sims = [pic.Simulation(cfg_of(w), stream=stream) for w in ws]
         n0 = sum(s.info().n_alive for s in sims)
         # warm-up (graphs, attributes, batch graph capture)
         if mode == "plain":
@@ -358,6 +382,8 @@ def run_batch(args):
             "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch2d_{len(ws)}", "sims": len(ws), "cells": cells,
+                       "tiles": {"push_tile": tile[:2], "chunk": chunk, "autotuned_on": ws[0].name}
+                       if args.autotune > 0 else "defaults",
                        "particles": int(sum(w.n_particles for w in ws)),
                        "sample": f"steps {args.warmup}..{args.warmup + K} of each 500-step run"},
             "plain": out["plain"], "batched": out["batched"], "batched_over_plain": ratio}
@@ -431,6 +457,8 @@ def run_serve(args):
 
 def main():
     args = parse()
+    global SCALE
+    SCALE = max(1, args.scale)
     if args.workload == "batch":
         args.steps = args.steps if args.steps > 0 else 100
         print(json.dumps(run_batch(args)))

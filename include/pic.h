@@ -100,6 +100,9 @@ typedef struct {
     uint64_t seed;           /* SplitMix64 seed of the slab positions */
     int64_t max_particles;   /* particle capacity; 0: slab count (pic_set_particles may need more) */
     int64_t max_exits;       /* exit-record capacity; 0: max_particles */
+    int32_t chunk;           /* particles per push work item (multiple of 256, 256..16384); 0: default */
+    int32_t autotune_steps;  /* > 0: pic_init first runs pic_autotune with this many trial steps
+                                for a tile or chunk left at 0 (cached per shape) */
 } pic_config;
 
 /* Host-side derived quantities (pic_derive_params, pic_info). */
@@ -109,7 +112,8 @@ typedef struct {
     int64_t n_particles;     /* seeded slab particles */
     int64_t device_bytes;    /* device memory pic_init will request */
     int32_t tile[3];         /* particle tile after autotuning */
-    int32_t yee_tile[3];     /* field-solver tile */
+    int32_t yee_tile[3];     /* field-solver tile (3D: x, y of a column and its segment in z) */
+    int32_t chunk;           /* particles per push work item */
 } pic_params;
 
 typedef struct {
@@ -145,6 +149,21 @@ pic_status pic_derive_params(const pic_config* cfg, pic_params* out);
  * top 24 bits / 2^24), zeroes the scattered field and captures the step as a CUDA
  * graph.  Synchronous on `stream`.  *out is NULL on failure. */
 pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* stream, pic_sim** out);
+
+/* Autotuner of the particle tile and the push work-item size (no counterpart in the paper:
+ * a layout choice of this implementation).  For each candidate (tiles of 8..32 cells per
+ * axis by dimension, then work items of 1024..4096 particles at the best tile) it creates
+ * the simulation on the current device, moves its clock to the pulse's arrival at the
+ * focus (LP/RP) so that the incident field is live at the particles, takes trial_steps
+ * untimed and trial_steps timed steps (CUDA events on `stream`) and destroys it; one
+ * candidate holds device memory at a time.  Candidates that do not fit (shared memory,
+ * device memory) are skipped.  On success cfg->tile and cfg->chunk hold the fastest
+ * choice and *ms_per_step (may be NULL) its time per step.  Only tile/chunk entries left
+ * at 0 are tuned.  Results are cached for the process per (dim, precision, n, ppc, beam,
+ * slab): a repeated call returns the cached choice without measuring.
+ * Errors: PIC_EINVAL (bad config, trial_steps < 1), PIC_ENODEV, or the first candidate's
+ * pic_init error when no candidate could be created. */
+pic_status pic_autotune(pic_config* cfg, int trial_steps, void* stream, double* ms_per_step);
 
 /* Advances n_steps >= 0 steps (one step: push + current deposition, particle re-sort,
  * field update).  Asynchronous on `stream` (graph replays). */

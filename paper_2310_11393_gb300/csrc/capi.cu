@@ -150,7 +150,7 @@ pic_status fail(pic_sim* s, pic_status st, const char* fmt, ...)
 
 struct Layout {
     int dim, es;
-    int n[3], na[3], pt[3], npt[3], pb[3], yt[3], nyt[3], yb[3];
+    int n[3], na[3], pt[3], npt[3], pb[3], yt[3], nyt[3], yb[3], yo[3];
     long long sy, sz, sc, natot;
     int nptiles, nytiles;
     long long cap, max_exits, nslab;
@@ -193,6 +193,9 @@ pic_status validate(const pic_config* c, pic_sim* s)
     for (int d = 0; d < c->dim; ++d)
         if (c->tile[d] < 0 || (c->tile[d] > 0 && (c->tile[d] > 248 || (d == 0 && c->tile[d] % 4))))
             return fail(s, PIC_EINVAL, "tile[%d] = %d invalid (x a multiple of 4, <= 248)", d, c->tile[d]);
+    if (c->chunk < 0 || (c->chunk > 0 && (c->chunk % 256 || c->chunk > 16384)))
+        return fail(s, PIC_EINVAL, "chunk = %d invalid (a multiple of 256, <= 16384)", c->chunk);
+    if (c->autotune_steps < 0) return fail(s, PIC_EINVAL, "autotune_steps must be >= 0");
     int bits = 0;
     for (int d = 0; d < c->dim; ++d) bits += bits_for(c->n[d]);
     if (bits > 31) return fail(s, PIC_EINVAL, "grid too large for the packed cell index");
@@ -209,7 +212,15 @@ void choose_tiles(const pic_config* c, int pt[3], int yt[3])
     } else if (c->dim == 2) {
         pt[0] = 16; pt[1] = 16; yt[0] = 32; yt[1] = 16;
     } else {
-        pt[0] = 8; pt[1] = 8; pt[2] = 8; yt[0] = 8; yt[1] = 8; yt[2] = 8;
+        // columns of Y3_PX x Y3_PY marching along z in segments: at least ~600 work items
+        // (a few per resident block on a full GPU), segments of at most 64 planes
+        pt[0] = 8; pt[1] = 8; pt[2] = 8;
+        yt[0] = Y3_PX; yt[1] = Y3_PY;
+        const long long ncol = (long long)ceil_div(c->n[0] + 1, Y3_PX) * ceil_div(c->n[1] + 1, Y3_PY);
+        const int nz = c->n[2] + 1;
+        int nseg = std::max<int>(ceil_div(nz, 64), (int)std::min<long long>(nz, (600 + ncol - 1) / ncol));
+        nseg = std::min(nseg, std::max(1, nz / 8));
+        yt[2] = ceil_div(nz, nseg);
     }
     for (int d = c->dim; d < 3; ++d) pt[d] = yt[d] = 1;
     for (int d = 0; d < c->dim; ++d)
@@ -230,6 +241,8 @@ Layout make_layout(const pic_config* c)
             L.nyt[d] = ceil_div(N + 1, L.yt[d]);
             L.pb[d] = d == 0 ? L.pt[d] + 8 : L.pt[d] + 5;
             L.yb[d] = d == 0 ? L.yt[d] + 8 : L.yt[d] + 4;
+            L.yo[d] = L.yt[d];
+            if (c->dim == 3 && d == 2) L.yb[d] = L.yo[d] = 1;     // one plane per load / store
             long long need = N + 1 + 2 * G;
             if (d == 0) {
                 need = std::max<long long>(need, (long long)L.npt[d] * L.pt[d] + 8);
@@ -241,7 +254,8 @@ Layout make_layout(const pic_config* c)
             }
             L.na[d] = (int)need;
         } else {
-            L.n[d] = 1; L.na[d] = 1; L.npt[d] = 1; L.nyt[d] = 1; L.pb[d] = 1; L.yb[d] = 1; L.pt[d] = 1; L.yt[d] = 1;
+            L.n[d] = 1; L.na[d] = 1; L.npt[d] = 1; L.nyt[d] = 1; L.pb[d] = 1; L.yb[d] = 1; L.yo[d] = 1;
+            L.pt[d] = 1; L.yt[d] = 1;
         }
     }
     L.sy = L.na[0];
@@ -257,13 +271,15 @@ Layout make_layout(const pic_config* c)
     }
     L.cap = c->max_particles > 0 ? c->max_particles : std::max<long long>(L.nslab, 1);
     L.max_exits = c->max_exits > 0 ? c->max_exits : L.cap;
-    L.chunk = 2048;
+    L.chunk = c->chunk > 0 ? c->chunk : 2048;
     L.max_chunks = (int)(L.nptiles + (L.cap + L.chunk - 1) / L.chunk + 1);
     const long long pbv = (long long)L.pb[0] * L.pb[1] * L.pb[2];
     const long long ybv = (long long)L.yb[0] * L.yb[1] * L.yb[2];
     const long long ytv = (long long)L.yt[0] * L.yt[1] * L.yt[2];
     L.push_smem = round128((size_t)(6 * pbv * L.es)) + (size_t)(3 * pbv * L.es);
-    L.yee_smem = round128(round128((size_t)(6 * ybv * L.es)) + (size_t)(3 * ybv * L.es)) + (size_t)(6 * ytv * L.es);
+    L.yee_smem = c->dim == 3 ? yee3_smem(L.es)
+                             : round128(round128((size_t)(6 * ybv * L.es)) + (size_t)(3 * ybv * L.es)) +
+                                   (size_t)(6 * ytv * L.es);
     size_t b = 0;
     b += align256(sizeof(SimDev)) + align256(sizeof(DevState));
     b += align256((size_t)NFCOMP * L.natot * L.es);
@@ -309,6 +325,7 @@ pic_status derive(const pic_config* c, pic_params* out, pic_sim* s)
         p.tile[d] = L.pt[d];
         p.yee_tile[d] = L.yt[d];
     }
+    p.chunk = L.chunk;
     *out = p;
     return PIC_OK;
 }
@@ -469,13 +486,20 @@ const char* pic_last_error(const pic_sim* sim)
     return g_thread_err.c_str();
 }
 
-pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* stream, pic_sim** out)
+pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* stream, pic_sim** out)
 {
     if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
     *out = nullptr;
     pic_params prm;
-    pic_status r = derive(cfg, &prm, nullptr);
+    pic_status r = derive(cfg_in, &prm, nullptr);
     if (r != PIC_OK) return r;
+    pic_config tuned = *cfg_in;
+    if (cfg_in->autotune_steps > 0) {
+        tuned.autotune_steps = 0;
+        if ((r = pic_autotune(&tuned, cfg_in->autotune_steps, stream, nullptr)) != PIC_OK) return r;
+        if ((r = derive(&tuned, &prm, nullptr)) != PIC_OK) return r;
+    }
+    const pic_config* cfg = &tuned;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PIC_ENODEV, "no CUDA device");
     cudaDeviceProp prop;
@@ -585,7 +609,7 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
         (r = make_map(s, &h.tm_pj, L, L.pb, 3)) != PIC_OK ||
         (r = make_map(s, &h.tm_yin, L, L.yb, 6)) != PIC_OK ||
         (r = make_map(s, &h.tm_yj, L, L.yb, 3)) != PIC_OK ||
-        (r = make_map(s, &h.tm_yout, L, L.yt, 6)) != PIC_OK) {
+        (r = make_map(s, &h.tm_yout, L, L.yo, 6)) != PIC_OK) {
         std::string m = s->err;
         pic_destroy(s);
         return fail(nullptr, r, "%s", m.c_str());

@@ -1,0 +1,152 @@
+// Autotuner of the particle tile and the push work-item size (pic_autotune).
+//
+// The push kernel stages one tile's field box in shared memory per work item, so the tile
+// sets the box's halo overhead, the shared memory per block (and with it the blocks per SM)
+// and the particles that share a box; the work-item size sets the load balance across the
+// SMs.  The best pair depends on the dimension, the precision, the particles per cell and
+// the beam, so it is measured: every candidate is run for a few steps at the time the
+// pulse reaches the focus, and the fastest is kept (cached per shape for the process).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pic.h"
+
+namespace {
+
+struct Choice {
+    int tile[3];
+    int chunk;
+    double ms;
+};
+
+std::mutex g_mu;
+std::map<std::string, Choice> g_cache;
+
+std::string key_of(const pic_config* c)
+{
+    char b[256];
+    snprintf(b, sizeof b, "%d|%d|%d,%d,%d|%d|%d|%d,%d,%d|%d,%d,%d|%d,%d,%d|%d", c->dim, c->precision, c->n[0], c->n[1],
+             c->n[2], c->ppc, c->beam, c->slab_lo[0], c->slab_lo[1], c->slab_lo[2], c->slab_hi[0], c->slab_hi[1],
+             c->slab_hi[2], c->tile[0], c->tile[1], c->tile[2], c->chunk);
+    return b;
+}
+
+std::vector<std::vector<int>> tile_candidates(int dim)
+{
+    if (dim == 1) return {{32, 1, 1}, {64, 1, 1}, {128, 1, 1}, {16, 1, 1}};
+    if (dim == 2) return {{16, 16, 1}, {32, 16, 1}, {16, 8, 1}, {32, 32, 1}, {8, 8, 1}};
+    return {{8, 8, 8}, {16, 8, 8}, {8, 8, 4}, {16, 8, 4}, {8, 4, 4}};
+}
+
+// time per step of one candidate, or a negative pic_status
+double trial(const pic_config& c, int steps, cudaStream_t st, pic_status* err)
+{
+    pic_sim* s = nullptr;
+    pic_status r = pic_init(&c, nullptr, st, &s);
+    if (r != PIC_OK) {
+        *err = r;
+        return -1.0;
+    }
+    pic_params p;
+    pic_derive_params(&c, &p);
+    if ((c.beam == PIC_BEAM_LP || c.beam == PIC_BEAM_RP) && p.dt > 0) {
+        const long long k = std::max<long long>(0, std::llround(c.t_focus / p.dt) - steps);
+        pic_set_step(s, k, st);
+    }
+    double ms = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (pic_step(s, steps, st) == PIC_OK && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess &&
+        pic_step(s, steps, st) == PIC_OK && cudaEventRecord(e1, st) == cudaSuccess &&
+        cudaEventSynchronize(e1) == cudaSuccess) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t / steps;
+    }
+    pic_info inf;
+    if (ms > 0 && pic_info_get(s, &inf, st) == PIC_OK && (inf.status & PIC_FLAG_TIMEOUT)) ms = -1.0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    pic_destroy(s);
+    *err = ms > 0 ? PIC_OK : PIC_ECUDA;
+    return ms;
+}
+
+}  // namespace
+
+extern "C" pic_status pic_autotune(pic_config* cfg, int trial_steps, void* stream, double* ms_per_step)
+{
+    if (!cfg || trial_steps < 1) return PIC_EINVAL;
+    pic_params p;
+    pic_status r = pic_derive_params(cfg, &p);
+    if (r != PIC_OK) return r;
+    const bool tune_tile = cfg->tile[0] == 0 && (cfg->dim < 2 || cfg->tile[1] == 0) && (cfg->dim < 3 || cfg->tile[2] == 0);
+    const bool tune_chunk = cfg->chunk == 0;
+    if (!tune_tile && !tune_chunk) {
+        if (ms_per_step) *ms_per_step = 0.0;
+        return PIC_OK;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PIC_ENODEV;
+    const std::string key = std::to_string(dev) + "#" + key_of(cfg);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            for (int d = 0; d < 3; ++d) cfg->tile[d] = it->second.tile[d];
+            cfg->chunk = it->second.chunk;
+            if (ms_per_step) *ms_per_step = it->second.ms;
+            return PIC_OK;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    pic_config c = *cfg;
+    c.autotune_steps = 0;
+    Choice best{{cfg->tile[0], cfg->tile[1], cfg->tile[2]}, cfg->chunk, -1.0};
+    pic_status first_err = PIC_OK;
+    auto consider = [&](const pic_config& cand) {
+        pic_status e = PIC_OK;
+        const double ms = trial(cand, trial_steps, st, &e);
+        if (ms > 0 && (best.ms < 0 || ms < best.ms)) {
+            best.ms = ms;
+            for (int d = 0; d < 3; ++d) best.tile[d] = cand.tile[d];
+            best.chunk = cand.chunk;
+        } else if (ms <= 0 && first_err == PIC_OK) {
+            first_err = e;
+        }
+        cudaGetLastError();      // a candidate that failed leaves no sticky error behind
+    };
+    // tiles first (work items at the default size), then work-item sizes at the best tile
+    if (tune_tile) {
+        for (const auto& t : tile_candidates(cfg->dim)) {
+            pic_config cand = c;
+            for (int d = 0; d < 3; ++d) cand.tile[d] = d < cfg->dim ? t[d] : 0;
+            if (tune_chunk) cand.chunk = 0;
+            consider(cand);
+        }
+    } else {
+        consider(c);
+    }
+    if (best.ms < 0) return first_err != PIC_OK ? first_err : PIC_ECUDA;
+    if (tune_chunk) {
+        best.chunk = 2048;      // the measurements above ran at the default size
+        for (int ch : {1024, 4096}) {
+            pic_config cand = c;
+            for (int d = 0; d < 3; ++d) cand.tile[d] = best.tile[d];
+            cand.chunk = ch;
+            consider(cand);
+        }
+    }
+    for (int d = 0; d < 3; ++d) cfg->tile[d] = best.tile[d];
+    cfg->chunk = best.chunk;
+    if (ms_per_step) *ms_per_step = best.ms;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key] = best;
+    return PIC_OK;
+}

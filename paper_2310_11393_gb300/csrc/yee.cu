@@ -252,7 +252,285 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
     if (tid == 0) bulk_wait0();
 }
 
-// field-solver tiles per dimension (must match the host's tile choice)
+// ---------------------------------------------------------------------------------
+// 3D: a work item is a column of PX x PY points (x, y) over a segment [z0, z1) of planes.
+// The column marches along z; plane k of E, B and J_p (box x: 4 points of halo on each
+// side, y: 2 below and 1 above) arrives by TMA into a ring of NS stages.  With
+//   A(k): Bh = B^{n+1/2} on plane k     (forward differences; planes k, k+1)
+//   B(k): N  = E^{n+1}   on plane k     (backward differences; Bh of planes k, k-1),
+//         then the Mur faces of plane k (plane 0: once N(1) exists)
+//   D(k): B^{n+1} on plane k from Bh(k), N(k), N(k+1); E^{n+1}, B^{n+1} of plane k leave
+//         by one TMA store (double-buffered) and J_{1-p} of plane k is cleared,
+// iteration q runs A(q+1) together with D(q-1), then B(q+1): two barriers per plane.
+// Bh is kept for x in [x0-2, x0+PX], y in [y0-2, y0+PY]; N for x in [x0-1, x0+PX],
+// y in [y0-1, y0+PY] and planes from z0-1: one more than the outputs need on the low
+// side, so that every face point's Mur neighbour (one point inwards) is on hand.
+// ---------------------------------------------------------------------------------
+template <typename R, int PX, int PY, int NS, int NT>
+__global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+                                              int nwork, int* __restrict__ counter)
+{
+    constexpr int TV = PX * PY;
+    constexpr int BX = PX + 8, BY = PY + 4, BV = BX * BY;
+    constexpr size_t STAGE = round128(9 * BV * sizeof(R));
+    constexpr size_t JOFF = round128(6 * BV * sizeof(R));
+    constexpr size_t HOFF = NS * STAGE;
+    constexpr size_t NOFF = HOFF + round128(9 * BV * sizeof(R));
+    constexpr size_t OOFF = NOFF + round128(6 * BV * sizeof(R));
+    constexpr int AW = PX + 3, AH = PY + 3;      // Bh range: box x 2 .. PX+4, y 0 .. PY+2
+    constexpr int NW = PX + 2, NH = PY + 2;      // N range:  box x 3 .. PX+4, y 1 .. PY+2
+    static_assert(NT >= TV && NT >= NW * NH, "one pass of B and D per plane");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[NS];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto In = [&](int stage) { return reinterpret_cast<R*>(smem_raw + stage * STAGE); };   // [9][BY][BX]
+    R* Hr = reinterpret_cast<R*>(smem_raw + HOFF);     // [3][3][BY][BX]  Bh ring
+    R* Nr = reinterpret_cast<R*>(smem_raw + NOFF);     // [2][3][BY][BX]  N ring
+    R* Outb = reinterpret_cast<R*>(smem_raw + OOFF);   // [2][6][PY][PX]
+    uint32_t ph = 0;      // mbarrier phase of each stage
+    int oslot = 0;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nwork) break;
+        const Work wk = work[item];
+        const SimDev& S = sims[wk.sim];
+        DevState* st = S.st;
+        const int par = st->parity;
+        int t = wk.tile;
+        const int cx = t % S.nyt[0];
+        t /= S.nyt[0];
+        const int cy = t % S.nyt[1];
+        const int cz = t / S.nyt[1];
+        const int x0 = cx * PX, y0 = cy * PY;
+        const int z0 = cz * S.yt[2];
+        const int z1 = min(z0 + S.yt[2], S.n[2] + 1);
+        const int pa = z0 - 2, plast = z1 + 1;     // planes loaded
+        const bool col_int = x0 > 0 && x0 + PX < S.n[0] && y0 > 0 && y0 + PY < S.n[1];
+        const YeeC<R>& yc = yee_of<R>(S);
+        const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
+        auto stage_of = [&](int p) { return (p - pa) % NS; };
+        auto Hs = [&](int p) { return Hr + ((p - pa) % 3) * 3 * BV; };
+        auto Ns = [&](int p) { return Nr + ((p - pa) & 1) * 3 * BV; };
+        auto issue = [&](int p) {
+            const int sgi = stage_of(p);
+            const int org[3] = {x0 - 4 + G, y0 - 2 + G, p + G};
+            mbar_arrive_expect_tx(&bars[sgi], (unsigned)(9 * BV * sizeof(R)));
+            tma_load_box<3>(In(sgi), &S.tm_yin, org, comp_eb(par), &bars[sgi]);
+            tma_load_box<3>(reinterpret_cast<unsigned char*>(In(sgi)) + JOFF, &S.tm_yj, org, comp_j(par), &bars[sgi]);
+        };
+        if (tid == 0) {
+            tensormap_acquire(&S.tm_yin);
+            tensormap_acquire(&S.tm_yj);
+            tensormap_acquire(&S.tm_yout);
+            for (int p = pa; p <= min(pa + NS - 1, plast); ++p) issue(p);
+        }
+        int pissued = min(pa + NS - 1, plast);
+        int pw = pa - 1;      // last plane waited for
+
+        // Mur faces of plane m (every point of the N range on a face, fewer faces first).
+        // Off the z faces only the lines x = 0, n_x and y = 0, n_y of the column are visited
+        // (a point on two lines is written twice, with the same value).
+        auto mur_plane = [&](int m) {
+            const R* Im = In(stage_of(m));
+            R* Nm = Ns(m);
+            int fx[2], fy[2], nfx = 0, nfy = 0;
+            if (4 - x0 >= 3) fx[nfx++] = 4 - x0;
+            if (S.n[0] - x0 + 4 <= PX + 4) fx[nfx++] = S.n[0] - x0 + 4;
+            if (2 - y0 >= 1) fy[nfy++] = 2 - y0;
+            if (S.n[1] - y0 + 2 <= PY + 2) fy[nfy++] = S.n[1] - y0 + 2;
+            const bool zf = m == 0 || m == S.n[2];
+            const int npass = (nfx > 0) + (nfy > 0) + (zf ? 1 : 0);
+            const int ncand = zf ? NW * NH : nfx * NH + nfy * NW;
+            for (int pass = 1; pass <= npass; ++pass) {
+                for (int k = tid; k < ncand; k += NT) {
+                    int lx, ly;
+                    if (zf) {
+                        lx = 3 + k % NW;
+                        ly = 1 + k / NW;
+                    } else if (k < nfx * NH) {
+                        lx = fx[k / NH];
+                        ly = 1 + k % NH;
+                    } else {
+                        const int r = k - nfx * NH;
+                        ly = fy[r / NW];
+                        lx = 3 + r % NW;
+                    }
+                    const int i = lx + BX * ly;
+                    const int g[3] = {x0 - 4 + lx, y0 - 2 + ly, m};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int fm = face_axes<3>(S, c, g);
+                        if (!fm || __popc(fm) != pass) continue;
+                        const int a = __ffs(fm) - 1;
+                        const int dir = (g[a] == 0) ? 1 : -1;
+                        R eo_nb, en_nb;
+                        if (a < 2) {
+                            const int nb = i + dir * (a == 0 ? 1 : BX);
+                            eo_nb = Im[c * BV + nb];
+                            en_nb = Nm[c * BV + nb];
+                        } else {
+                            eo_nb = In(stage_of(m + dir))[c * BV + i];
+                            en_nb = Ns(m + dir)[c * BV + i];
+                        }
+                        Nm[c * BV + i] = eo_nb + km * (en_nb - Im[c * BV + i]);
+                    }
+                }
+                __syncthreads();
+            }
+        };
+
+        bool failed = false;
+        for (int q = z0 - 3; q <= z1; ++q) {
+            bool ok = true;
+            while (pw < min(q + 2, plast)) {
+                ++pw;
+                const int sgi = stage_of(pw);
+                ok = ok && mbar_wait_bounded(&bars[sgi], (ph >> sgi) & 1u);
+                ph ^= 1u << sgi;
+            }
+            // S1: A(q+1) and D(q-1)
+            const bool doA = q + 1 <= z1, doD = q - 1 >= z0;
+            if (doA || doD) {
+                const int m = q - 1;
+                for (int u = tid; u < TV + AW * AH; u += NT) {
+                    if (u < TV) {
+                        if (!doD) continue;
+                        const R* H0 = Hs(m);
+                        const R* N0 = Ns(m);
+                        const R* N1 = Ns(m + 1);
+                        const int tx = u % PX, ty = u / PX;
+                        const int i = (tx + 4) + BX * (ty + 2);
+                        const R dNz_dy = N0[2 * BV + i + BX] - N0[2 * BV + i];
+                        const R dNx_dy = N0[i + BX] - N0[i];
+                        const R dNy_dz = N1[BV + i] - N0[BV + i];
+                        const R dNx_dz = N1[i] - N0[i];
+                        const R dNz_dx = N0[2 * BV + i + 1] - N0[2 * BV + i];
+                        const R dNy_dx = N0[BV + i + 1] - N0[BV + i];
+                        R v[6] = {N0[i], N0[BV + i], N0[2 * BV + i], H0[i] - hc * (dNz_dy - dNy_dz),
+                                  H0[BV + i] - hc * (dNx_dz - dNz_dx), H0[2 * BV + i] - hc * (dNy_dx - dNx_dy)};
+                        if (!(col_int && m >= 1 && m <= S.n[2] - 1)) {
+                            const int g[3] = {x0 + tx, y0 + ty, m};
+#pragma unroll
+                            for (int c = 0; c < 6; ++c)
+                                if (!has_point<3>(S, c, g)) v[c] = R(0);
+                        }
+                        R* Out = Outb + oslot * 6 * TV;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) Out[c * TV + u] = v[c];
+                        // clear J_{1-p} on plane m (the next step deposits into it)
+                        R* Fg = reinterpret_cast<R*>(S.F);
+                        const long long jb = (long long)comp_j(1 - par) * S.sc + (long long)(m + G) * S.sz +
+                                             (long long)(y0 + ty + G) * S.sy + (x0 + tx + G);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Fg[jb + c * S.sc] = R(0);
+                    } else {
+                        if (!doA) continue;
+                        const int k = u - TV;
+                        const R* I0 = In(stage_of(q + 1));
+                        const R* I1 = In(stage_of(q + 2));
+                        R* Hc = Hs(q + 1);
+                        const int lx = 2 + k % AW, ly = k / AW;
+                        const int i = lx + BX * ly;
+                        const R dEz_dy = I0[2 * BV + i + BX] - I0[2 * BV + i];
+                        const R dEx_dy = I0[i + BX] - I0[i];
+                        const R dEy_dz = I1[BV + i] - I0[BV + i];
+                        const R dEx_dz = I1[i] - I0[i];
+                        const R dEz_dx = I0[2 * BV + i + 1] - I0[2 * BV + i];
+                        const R dEy_dx = I0[BV + i + 1] - I0[BV + i];
+                        Hc[i] = I0[3 * BV + i] - hc * (dEz_dy - dEy_dz);
+                        Hc[BV + i] = I0[4 * BV + i] - hc * (dEx_dz - dEz_dx);
+                        Hc[2 * BV + i] = I0[5 * BV + i] - hc * (dEy_dx - dEx_dy);
+                    }
+                }
+            }
+            if (doD) fence_proxy_async_smem();
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            if (doD) {
+                if (tid == 0) {
+                    const int oc[3] = {x0 + G, y0 + G, q - 1 + G};
+                    tma_store_box<3>(&S.tm_yout, oc, comp_eb(1 - par), Outb + oslot * 6 * TV);
+                    bulk_commit();
+                }
+                oslot ^= 1;
+            }
+            // S2: B(q+1), then its Mur faces
+            const int b = q + 1;
+            if (b >= z0 - 1 && b <= z1) {
+                const bool faces = !col_int || b == 0 || b == S.n[2];
+                const R* I0 = In(stage_of(b));
+                const R* J0 = I0 + JOFF / sizeof(R);
+                const R* Hc = Hs(b);
+                const R* Hp = Hs(b - 1);
+                R* Nc = Ns(b);
+                for (int k = tid; k < NW * NH; k += NT) {
+                    const int lx = 3 + k % NW, ly = 1 + k / NW;
+                    const int i = lx + BX * ly;
+                    const R dBz_dy = Hc[2 * BV + i] - Hc[2 * BV + i - BX];
+                    const R dBx_dy = Hc[i] - Hc[i - BX];
+                    const R dBy_dz = Hc[BV + i] - Hp[BV + i];
+                    const R dBx_dz = Hc[i] - Hp[i];
+                    const R dBz_dx = Hc[2 * BV + i] - Hc[2 * BV + i - 1];
+                    const R dBy_dx = Hc[BV + i] - Hc[BV + i - 1];
+                    const R ex = I0[i] + cdt * (dBz_dy - dBy_dz) - dt * J0[i];
+                    const R ey = I0[BV + i] + cdt * (dBx_dz - dBz_dx) - dt * J0[BV + i];
+                    const R ez = I0[2 * BV + i] + cdt * (dBy_dx - dBx_dy) - dt * J0[2 * BV + i];
+                    if (!faces) {
+                        Nc[i] = ex;
+                        Nc[BV + i] = ey;
+                        Nc[2 * BV + i] = ez;
+                    } else {
+                        const int g[3] = {x0 - 4 + lx, y0 - 2 + ly, b};
+                        if (!face_axes<3>(S, 0, g)) Nc[i] = ex;
+                        if (!face_axes<3>(S, 1, g)) Nc[BV + i] = ey;
+                        if (!face_axes<3>(S, 2, g)) Nc[2 * BV + i] = ez;
+                    }
+                }
+                // the store of two planes back has read its buffer (reused by the next D)
+                if (tid == 0) bulk_wait_read1();
+                __syncthreads();
+                if (faces && b != 0) mur_plane(b);
+                if (b == 1 && z0 <= 1) mur_plane(0);
+            } else {
+                if (tid == 0) bulk_wait_read1();
+                __syncthreads();
+            }
+            // plane q is no longer read: its stage takes plane q+NS
+            if (q >= pa && q + NS <= plast) {
+                if (tid == 0) issue(q + NS);
+                pissued = q + NS;
+            }
+        }
+        if (failed) {
+            if (tid == 0) {
+                atomicOr(&st->status, (unsigned)FLAG_TIMEOUT);
+                // let the loads still in flight land before the block exits
+                while (pw < pissued) {
+                    ++pw;
+                    const int sgi = stage_of(pw);
+                    mbar_wait_bounded(&bars[sgi], (ph >> sgi) & 1u);
+                    ph ^= 1u << sgi;
+                }
+                bulk_wait0();
+            }
+            return;
+        }
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+// 1D/2D field-solver tiles (must match the host's tile choice)
 template <int D>
 struct YeeTile;
 template <>
@@ -263,24 +541,30 @@ template <>
 struct YeeTile<2> {
     static constexpr int X = 32, Y = 16, Z = 1;
 };
-template <>
-struct YeeTile<3> {
-    static constexpr int X = 8, Y = 8, Z = 8;
-};
 
 template <int D, typename R>
 static void yee_t(const Group& g, cudaStream_t s)
 {
-    k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
-        <<<g.yee_grid, 256, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    if constexpr (D == 3)
+        k_yee3s<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>
+            <<<g.yee_grid, Y3_NT, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    else
+        k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
+            <<<g.yee_grid, 256, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
 }
 
 template <int D, typename R>
 static void attr_yee(size_t smem, int* out)
 {
-    auto k = k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, 256, smem);
+    if constexpr (D == 3) {
+        auto k = k_yee3s<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, Y3_NT, smem);
+    } else {
+        auto k = k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, 256, smem);
+    }
 }
 
 #define SFF_DISPATCH2(dim, prec, FN, ...)                       \

@@ -33,14 +33,14 @@ class pic_config(Structure):
         ("focus", c_double * 3), ("a_param", c_double), ("s_param", c_double), ("psi0", c_double),
         ("e_unif", c_double * 3), ("b_unif", c_double * 3), ("slab_lo", c_int32 * 3), ("slab_hi", c_int32 * 3),
         ("n_e", c_double), ("ppc", c_int32), ("tile", c_int32 * 3), ("seed", c_uint64),
-        ("max_particles", c_int64), ("max_exits", c_int64),
+        ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("autotune_steps", c_int32),
     ]
 
 
 class pic_params(Structure):
     _fields_ = [("a", c_double), ("s", c_double), ("psi0", c_double), ("dt", c_double),
                 ("n_particles", c_int64), ("device_bytes", c_int64), ("tile", c_int32 * 3),
-                ("yee_tile", c_int32 * 3)]
+                ("yee_tile", c_int32 * 3), ("chunk", c_int32)]
 
 
 class pic_info(Structure):
@@ -112,6 +112,8 @@ def load():
     L.pic_histogram_static.argtypes = [P, c_int, c_double, c_int, DP, P]
     L.pic_eval_incident.restype = c_int
     L.pic_eval_incident.argtypes = [P, c_int64, DP, DP, P]
+    L.pic_autotune.restype = c_int
+    L.pic_autotune.argtypes = [POINTER(pic_config), c_int, P, POINTER(c_double)]
     L.pic_batch_step.restype = c_int
     L.pic_batch_step.argtypes = [POINTER(P), c_int, c_int, P]
     L.pic_serve_open.restype = c_int
@@ -228,6 +230,14 @@ def pic_eval_incident(sim, pts, stream=0) -> np.ndarray:
     return out
 
 
+def pic_autotune(cfg: pic_config, trial_steps: int = 4, stream=0) -> float:
+    """Fills cfg.tile / cfg.chunk (entries left at 0) with the fastest measured choice;
+    returns its time per step in ms (0 when nothing was left to tune)."""
+    ms = c_double()
+    check(load().pic_autotune(byref(cfg), int(trial_steps), c_void_p(stream), byref(ms)))
+    return ms.value
+
+
 def pic_batch_step(sims, n_steps: int, stream=0):
     arr = (c_void_p * len(sims))(*[s.value if isinstance(s, c_void_p) else s for s in sims])
     st = load().pic_batch_step(arr, len(sims), int(n_steps), c_void_p(stream))
@@ -285,7 +295,7 @@ def torch_allocator(device=None):
     return a
 
 
-def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0) -> pic_config:
+def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chunk=0, autotune_steps=0) -> pic_config:
     """pic_config for a workload description (attributes as synth.Workload)."""
     c = pic_config()
     c.dim = w.dim
@@ -317,6 +327,8 @@ def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0) -> p
     c.seed = w.seed
     c.max_particles = max_particles
     c.max_exits = max_exits
+    c.chunk = chunk
+    c.autotune_steps = autotune_steps
     return c
 
 

@@ -77,6 +77,8 @@ def test_counts_and_footprint(P):
     (dict(slab_lo=(1, 256, 0)), "slab"),
     (dict(tile=(6, 16, 1)), "tile"),
     (dict(n=(8, 1024, 1)), "n[0]"),
+    (dict(chunk=1000), "chunk"),
+    (dict(chunk=32768), "chunk"),
 ])
 def test_invalid_configs_are_rejected(P, bad, frag):
     w = synth.c2_2d_lp()
@@ -98,3 +100,16 @@ def test_lp_needs_two_dimensions(P):
     w = synth.c1_1d_plane().with_(beam=synth.BEAM_LP, w0=TWO_PI, a0=1.0)
     with pytest.raises(P.PicError):
         P.pic_derive_params(P.config_from(w))
+
+
+def test_work_item_size_and_tuner_arguments(P):
+    w = synth.c2_2d_lp()
+    assert P.pic_derive_params(P.config_from(w)).chunk == 2048
+    assert P.pic_derive_params(P.config_from(w, chunk=4096)).chunk == 4096
+    # nothing left to tune: no device needed, nothing measured
+    c = P.config_from(w, tile=(32, 16, 1), chunk=1024)
+    assert P.pic_autotune(c, 3) == 0.0
+    assert list(c.tile)[:2] == [32, 16] and c.chunk == 1024
+    with pytest.raises(P.PicError) as e:
+        P.pic_autotune(P.config_from(w), 0)
+    assert e.value.status == P.PIC_EINVAL
