@@ -545,6 +545,9 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.ctile[0] = (int*)A.take((size_t)L.max_chunks * 4);
     h.ctile[1] = (int*)A.take((size_t)L.max_chunks * 4);
     h.chunk = L.chunk;
+    h.lane_p = 8;
+    if (cfg->ppc > 0)
+        for (h.lane_p = 1; h.lane_p * 2 <= std::min(cfg->ppc, 8);) h.lane_p *= 2;
     h.max_chunks = L.max_chunks;
     h.tcnt = (int*)A.take((size_t)L.nptiles * 4);
     h.tcur = (int*)A.take((size_t)L.nptiles * 4);

@@ -198,11 +198,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
         const R hq = R(-0.5 * S.dt);                // q dt / 2
         const int hx[3] = {4, 2, 2};                // box halo below the tile per axis
 
-        // Rounds of 256 particles; within a round lane l of warp w takes particle 8 l + w, so
-        // the 32 lanes of a warp are spread over the round (and over cells: 8 particles per
-        // cell sit next to each other after the sort) rather than walking consecutive, often
-        // same-cell, particles: fewer same-address shared-memory atomics in the deposit.
-        const int q = (tid & 31) * 8 + (tid >> 5);
+        // Rounds of 256 particles.  With P particles per cell (1, 2, 4 or 8) sitting next to
+        // each other after the sort, lane l of warp w takes particle P l + (w mod P) of the
+        // round's (w div P)-th group of 32 P: the 32 lanes of a warp then sit in 32
+        // consecutive cells, so the same stencil node of the deposit and the gather is a
+        // different shared-memory word (mostly a different bank) in every lane.
+        const int P = S.lane_p, wq = tid >> 5;
+        const int q = (tid & 31) * P + (wq & (P - 1)) + 32 * P * (wq / P);
         for (int rb = p0; rb < p1; rb += nth) {
             const int p = rb + q;
             if (p >= p1) continue;
@@ -270,9 +272,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
             const R ig = R(1) / m_sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             const R v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
 
-            // ---- Esirkepov deposition of the move (shapes relative to the old nearest node) ----
-            R S0[3][5], DS[3][5];
-            int jb[3] = {0, 0, 0};
+            // ---- Esirkepov deposition of the move ----
+            // Per axis the old shape covers the old nearest node and its two neighbours; the
+            // new shape is shifted by sh in {-1, 0, 1} nodes (|move| < 1 cell), so both fit a
+            // window of four nodes starting one below the old support when sh = -1 and at it
+            // otherwise.  S0 / DS: old shape / shape change on that window.  Along the
+            // current's own axis the window's last partial sum is the total charge change,
+            // zero: three nodes carry that component.
+            R S0[3][4], DS[3][4];
+            int jw[3] = {0, 0, 0};
             R mv[3] = {R(0), R(0), R(0)};
 #pragma unroll
             for (int d = 0; d < D; ++d) {
@@ -285,18 +293,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
                 R w0[3], w1[3];
                 shape2(d0, w0);
                 shape2(d1, w1);
-                R s1[5] = {R(0), R(0), R(0), R(0), R(0)};
-                if (sh < 0) {
-                    s1[0] = w1[0]; s1[1] = w1[1]; s1[2] = w1[2];
-                } else if (sh == 0) {
-                    s1[1] = w1[0]; s1[2] = w1[1]; s1[3] = w1[2];
-                } else {
-                    s1[2] = w1[0]; s1[3] = w1[1]; s1[4] = w1[2];
-                }
-                S0[d][0] = R(0); S0[d][1] = w0[0]; S0[d][2] = w0[1]; S0[d][3] = w0[2]; S0[d][4] = R(0);
+                const bool lo = sh < 0, hi = sh > 0;
+                const R o0[4] = {lo ? R(0) : w0[0], lo ? w0[0] : w0[1], lo ? w0[1] : w0[2], lo ? w0[2] : R(0)};
+                const R n1[4] = {hi ? R(0) : w1[0], hi ? w1[0] : w1[1], hi ? w1[1] : w1[2], hi ? w1[2] : R(0)};
 #pragma unroll
-                for (int m = 0; m < 5; ++m) DS[d][m] = s1[m] - S0[d][m];
-                jb[d] = c[d] + h0 - 2 - T0[d] + hx[d];
+                for (int m = 0; m < 4; ++m) {
+                    S0[d][m] = o0[m];
+                    DS[d][m] = n1[m] - o0[m];
+                }
+                jw[d] = c[d] + h0 - (lo ? 2 : 1) - T0[d] + hx[d];
             }
             R* Jx = Js;
             R* Jy = Js + bvol;
@@ -306,84 +311,84 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
             if constexpr (D == 1) {
                 R acc = R(0);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < 3; ++a) {
                     acc += cw * DS[0][a];
-                    sm_add(&Jx[jb[0] + a], acc);
+                    sm_add(&Jx[jw[0] + a], acc);
                 }
 #pragma unroll
-                for (int a = 0; a < 5; ++a) {
+                for (int a = 0; a < 4; ++a) {
                     const R f = S0[0][a] + R(0.5) * DS[0][a];
-                    sm_add(&Jy[jb[0] + a], -wt * v[1] * f);
-                    sm_add(&Jz[jb[0] + a], -wt * v[2] * f);
+                    sm_add(&Jy[jw[0] + a], -wt * v[1] * f);
+                    sm_add(&Jz[jw[0] + a], -wt * v[2] * f);
                 }
             } else if constexpr (D == 2) {
 #pragma unroll
-                for (int b = 0; b < 5; ++b) {
+                for (int b = 0; b < 4; ++b) {
                     const R fy = S0[1][b] + R(0.5) * DS[1][b];
                     R acc = R(0);
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
+                    for (int a = 0; a < 3; ++a) {
                         acc += cw * DS[0][a] * fy;
-                        sm_add(&Jx[(jb[1] + b) * bx + jb[0] + a], acc);
+                        sm_add(&Jx[(jw[1] + b) * bx + jw[0] + a], acc);
                     }
                 }
 #pragma unroll
-                for (int a = 0; a < 5; ++a) {
+                for (int a = 0; a < 4; ++a) {
                     const R fx = S0[0][a] + R(0.5) * DS[0][a];
                     R acc = R(0);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
+                    for (int b = 0; b < 3; ++b) {
                         acc += cw * DS[1][b] * fx;
-                        sm_add(&Jy[(jb[1] + b) * bx + jb[0] + a], acc);
+                        sm_add(&Jy[(jw[1] + b) * bx + jw[0] + a], acc);
                     }
                 }
                 const R qv = -wt * v[2];
 #pragma unroll
-                for (int b = 0; b < 5; ++b)
+                for (int b = 0; b < 4; ++b)
 #pragma unroll
-                    for (int a = 0; a < 5; ++a) {
+                    for (int a = 0; a < 4; ++a) {
                         const R wz = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
                                      R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
-                        sm_add(&Jz[(jb[1] + b) * bx + jb[0] + a], qv * wz);
+                        sm_add(&Jz[(jw[1] + b) * bx + jw[0] + a], qv * wz);
                     }
             } else {
 #pragma unroll
-                for (int cc = 0; cc < 5; ++cc)
+                for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
-                    for (int b = 0; b < 5; ++b) {
+                    for (int b = 0; b < 4; ++b) {
                         const R fyz = S0[1][b] * S0[2][cc] + R(0.5) * DS[1][b] * S0[2][cc] +
                                       R(0.5) * S0[1][b] * DS[2][cc] + third * DS[1][b] * DS[2][cc];
                         R acc = R(0);
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
+                        for (int a = 0; a < 3; ++a) {
                             acc += cw * DS[0][a] * fyz;
-                            sm_add(&Jx[(jb[2] + cc) * bxy + (jb[1] + b) * bx + jb[0] + a], acc);
+                            sm_add(&Jx[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
 #pragma unroll
-                for (int cc = 0; cc < 5; ++cc)
+                for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
-                    for (int a = 0; a < 5; ++a) {
+                    for (int a = 0; a < 4; ++a) {
                         const R fxz = S0[0][a] * S0[2][cc] + R(0.5) * DS[0][a] * S0[2][cc] +
                                       R(0.5) * S0[0][a] * DS[2][cc] + third * DS[0][a] * DS[2][cc];
                         R acc = R(0);
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
+                        for (int b = 0; b < 3; ++b) {
                             acc += cw * DS[1][b] * fxz;
-                            sm_add(&Jy[(jb[2] + cc) * bxy + (jb[1] + b) * bx + jb[0] + a], acc);
+                            sm_add(&Jy[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
 #pragma unroll
-                for (int b = 0; b < 5; ++b)
+                for (int b = 0; b < 4; ++b)
 #pragma unroll
-                    for (int a = 0; a < 5; ++a) {
+                    for (int a = 0; a < 4; ++a) {
                         const R fxy = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
                                       R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
                         R acc = R(0);
 #pragma unroll
-                        for (int cc = 0; cc < 4; ++cc) {
+                        for (int cc = 0; cc < 3; ++cc) {
                             acc += cw * DS[2][cc] * fxy;
-                            sm_add(&Jz[(jb[2] + cc) * bxy + (jb[1] + b) * bx + jb[0] + a], acc);
+                            sm_add(&Jz[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
             }

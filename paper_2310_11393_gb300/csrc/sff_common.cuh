@@ -89,6 +89,7 @@ struct alignas(128) SimDev {
     int* coff[2];             // chunk offsets [nptiles + 1]: tile t owns chunks coff[t] .. coff[t+1]-1
     int* ctile[2];            // chunk -> tile map [max_chunks]
     int chunk;                // particles per chunk (the unit of work of push and scatter)
+    int lane_p;               // push lane stride: particles per cell rounded down to 1, 2, 4 or 8
     int max_chunks;
     int* tcnt;                // per-tile counts of the next step
     int* tcur;                // per-tile write cursors
