@@ -78,6 +78,19 @@ __device__ __forceinline__ bool negligible(const BeamC<R>& b, R lnw)
 __device__ __forceinline__ float m_exp_mag(float x) { return __expf(x); }   // error matters only near x = 0
 __device__ __forceinline__ double m_exp_mag(double x) { return exp(x); }
 
+// sin and cos of a phase of a few tens of radians: Cody-Waite reduction by 2 pi (2 pi split
+// into its float value and the float of the remainder; k <= 2^4 keeps k c1 within the
+// fused multiply-add's exact range) to |r| <= pi, then the SFU pair, whose absolute error
+// on [-pi, pi] is below 1e-6: the carrier phase keeps ~5e-7 absolute accuracy.
+__device__ __forceinline__ void sincos_phase(float x, float* s, float* c)
+{
+    const float k = rintf(x * 0.159154937f);
+    float r = fmaf(-k, 6.28318548f, x);
+    r = fmaf(-k, -1.74845553e-7f, r);
+    __sincosf(r, s, c);
+}
+__device__ __forceinline__ void sincos_phase(double x, double* s, double* c) { sincos(x, s, c); }
+
 // e^{i phi0} w^{-(s+1)}, w = 1 - i tau/s, and g^(1), g^(2) (Eq. poisson_dstr), given log|w|
 template <typename R>
 __device__ __forceinline__ void poisson3(const BeamC<R>& b, Cx<R> tau, R lnw, Cx<R>& g0, Cx<R>& g1, Cx<R>& g2)
@@ -86,7 +99,7 @@ __device__ __forceinline__ void poisson3(const BeamC<R>& b, Cx<R> tau, R lnw, Cx
     const R th = m_atan2(w.y, w.x);
     const R mag = m_exp_mag(-b.sp1 * lnw);
     R sn, cs;
-    m_sincos(b.phi0 - b.sp1 * th, &sn, &cs);
+    sincos_phase(b.phi0 - b.sp1 * th, &sn, &cs);
     g0 = {mag * cs, mag * sn};
     // q = i a/(s w)
     const R den = R(1) / (b.s * (w.x * w.x + w.y * w.y));

@@ -41,8 +41,9 @@ std::string key_of(const pic_config* c)
 std::vector<std::vector<int>> tile_candidates(int dim)
 {
     if (dim == 1) return {{32, 1, 1}, {64, 1, 1}, {128, 1, 1}, {16, 1, 1}};
-    if (dim == 2) return {{16, 16, 1}, {32, 16, 1}, {16, 8, 1}, {32, 32, 1}, {8, 8, 1}};
-    return {{8, 8, 8}, {16, 8, 8}, {8, 8, 4}, {16, 8, 4}, {8, 4, 4}};
+    // tiles 32 cells wide put a warp's 32 lanes (consecutive cells) on one row of the box
+    if (dim == 2) return {{16, 16, 1}, {32, 16, 1}, {16, 8, 1}, {32, 32, 1}, {8, 8, 1}, {64, 8, 1}, {64, 16, 1}};
+    return {{8, 8, 8}, {16, 8, 8}, {8, 8, 4}, {16, 8, 4}, {8, 4, 4}, {32, 4, 4}, {32, 4, 2}, {32, 8, 2}};
 }
 
 // time per step of one candidate, or a negative pic_status

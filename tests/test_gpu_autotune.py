@@ -11,8 +11,8 @@ from _support import momentum_error, field_errors, small_2d, small_3d
 
 pytestmark = pytest.mark.gpu
 
-TILES = {2: [(16, 16), (32, 16), (16, 8), (32, 32), (8, 8)],
-         3: [(8, 8, 8), (16, 8, 8), (8, 8, 4), (16, 8, 4), (8, 4, 4)]}
+TILES = {2: [(16, 16), (32, 16), (16, 8), (32, 32), (8, 8), (64, 8), (64, 16)],
+         3: [(8, 8, 8), (16, 8, 8), (8, 8, 4), (16, 8, 4), (8, 4, 4), (32, 4, 4), (32, 4, 2), (32, 8, 2)]}
 
 
 @pytest.fixture(scope="module")
