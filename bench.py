@@ -149,6 +149,25 @@ def bytes_per_push(w):
     return part + grid
 
 
+def shard(n, rank, world):
+    """Items of a batch taken by one rank (round robin): independent simulations need no
+    exchange between ranks, so the ranks are replicas over disjoint shares."""
+    return list(range(rank, n, world))
+
+
+def job_totals(pushes, secs, world, device=None):
+    """Whole-job pushes (sum over ranks) and time (max over ranks)."""
+    if world <= 1:
+        return pushes, secs
+    import torch
+
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    p = torch.tensor([pushes], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(p)
+    return float(p.item()), float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -195,15 +214,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     n_b = sim.info().n_alive
     pushes = 0.5 * (n_a + n_b) * args.steps
-    t_max = secs
-    tot_pushes = pushes
+    tot_pushes, t_max = job_totals(pushes, secs, world, dev)
     if world > 1:
-        t = torch.tensor([secs], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        p = torch.tensor([pushes], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(p)
-        tot_pushes = float(p.item())
         torch.distributed.barrier()
     info = sim.info()
     sim.close()
@@ -306,8 +318,19 @@ def cpu_baseline(w, nsteps):
             "seconds": t1 - t0}
 
 
+def reference_sample(w, max_particles=80_000):
+    """The workload on a box shrunk per axis (same cell size, physics and layout, slab and
+    focus scaled with the box) until its electrons fit max_particles: one oracle step of it
+    takes about 0.1 s, so --steps K of the full run's K stays within a few minutes."""
+    f = 1
+    while synth.scaled(w, f).n_particles > max_particles and f < 64:
+        f += 1
+    return synth.scaled(w, f) if f > 1 else w, f
+
+
 def run_reference(args, rank, world):
-    w = workload(args.workload)
+    full = workload(args.workload)
+    w, f = reference_sample(full)
     import oracle
 
     oracle.build()
@@ -319,16 +342,19 @@ def run_reference(args, rank, world):
     t1 = time.perf_counter()
     n1 = sim.num_particles()
     v = 0.5 * (n0 + n1) * args.steps / (t1 - t0)
+    what = f"full {w.name} workload" if f == 1 else f"{full.name} box divided by {f} per axis ({w.n_particles} electrons)"
     cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": f"full {w.name} workload, {args.steps} steps after {args.warmup} warm-up steps, FP64, 1 thread"}
+          "sample": f"{what}, {args.steps} steps after {args.warmup} warm-up steps, FP64, 1 thread"}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": (t1 - t0) / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "dim": w.dim, "grid": list(w.n[: w.dim]), "particles": w.n_particles},
+            "config": {"workload": full.name, "dim": full.dim, "grid": list(full.n[: full.dim]),
+                       "particles": full.n_particles, "sample_grid": list(w.n[: w.dim]),
+                       "sample_particles": w.n_particles},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_batch(args):
+def run_batch(args, rank=0, world=1, local_rank=0):
     """Batched 2D workload: `--sims` independent runs of uneven size (LP/RP mix).  The same
     K steps of every simulation are timed (a) one simulation after another, each through its
     own step graph, and (b) all together through pic_batch_step (one persistent launch per
@@ -338,8 +364,10 @@ def run_batch(args):
     from paper_2310_11393_gb300 import _build, pic
 
     _build.build()
-    torch.cuda.set_device(0)
-    ws = synth.c4_batch(args.sims)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ws_all = synth.c4_batch(args.sims)
+    ws = [ws_all[i] for i in shard(len(ws_all), rank, world)]
     stream = torch.cuda.current_stream().cuda_stream
     K = args.steps
     out = {}
@@ -373,18 +401,20 @@ def run_batch(args):
         torch.cuda.synchronize()
         secs = e0.elapsed_time(e1) * 1e-3
         n1 = sum(s.info().n_alive for s in sims)
-        out[mode] = {"pushes_per_s": 0.5 * (n0 + n1) * K / secs, "seconds": secs}
+        pushes, secs = job_totals(0.5 * (n0 + n1) * K, secs, world, dev)
+        out[mode] = {"pushes_per_s": pushes / secs, "seconds": secs}
         for s in sims:
             s.close()
-    cells = sum(w.n_cells for w in ws)
+    cells = sum(w.n_cells for w in ws_all)
     ratio = out["batched"]["pushes_per_s"] / out["plain"]["pushes_per_s"]
     return {"metric": "batched particle-pushes/s (256 uneven 2D runs)", "value": out["batched"]["pushes_per_s"],
-            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "higher_is_better": True,
+            "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "strong", "parallelism": f"replicas x{world}, simulations round robin" if world > 1 else "single GPU",
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch2d_{len(ws)}", "sims": len(ws), "cells": cells,
+            "config": {"workload": f"batch2d_{len(ws_all)}", "sims": len(ws_all), "cells": cells,
                        "tiles": {"push_tile": tile[:2], "chunk": chunk, "autotuned_on": ws[0].name}
                        if args.autotune > 0 else "defaults",
-                       "particles": int(sum(w.n_particles for w in ws)),
+                       "particles": int(sum(w.n_particles for w in ws_all)),
                        "sample": f"steps {args.warmup}..{args.warmup + K} of each 500-step run"},
             "plain": out["plain"], "batched": out["batched"], "batched_over_plain": ratio}
 
@@ -459,19 +489,12 @@ def main():
     args = parse()
     global SCALE
     SCALE = max(1, args.scale)
-    if args.workload == "batch":
-        args.steps = args.steps if args.steps > 0 else 100
-        print(json.dumps(run_batch(args)))
-        return
-    if args.workload == "serve":
-        print(json.dumps(run_serve(args)))
-        return
-    if args.steps <= 0:
-        args.steps = workload(args.workload).steps
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if args.steps <= 0:
+            args.steps = workload(args.workload).steps
         if rank == 0:
             print(json.dumps(run_reference(args, rank, world)))
         return
@@ -480,6 +503,19 @@ def main():
 
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+    if args.workload in ("batch", "serve"):
+        if args.workload == "batch":
+            args.steps = args.steps if args.steps > 0 else 100
+            out = run_batch(args, rank, world, local_rank)
+        else:
+            out = run_serve(args)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    if args.steps <= 0:
+        args.steps = workload(args.workload).steps
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
         run_cb = world == 1 and not args.no_cpu_baseline
