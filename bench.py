@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "batch", "serve"])
     ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
-    ap.add_argument("--autotune", type=int, default=4,
+    ap.add_argument("--autotune", type=int, default=10,
                     help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
     ap.add_argument("--sims", type=int, default=256, help="batch: number of simulations")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")

@@ -55,7 +55,11 @@ inline BeamC<R> make_beam_consts(const SimDev& S)
     for (int d = 0; d < 3; ++d) {
         b.eu[d] = R(S.e_unif[d]);
         b.bu[d] = R(S.b_unif[d]);
+        b.frf[d] = R(S.frf[d]);
     }
+    b.hq = R(-0.5 * S.dt);
+    b.dtdx = R(S.dt * S.inv_dx);
+    b.jfac = R(S.dx / S.dt);
     return b;
 }
 
@@ -321,8 +325,8 @@ __device__ __forceinline__ void incident_at(const SimDev& S, const BeamC<R>& b, 
         const R inv_a = b.inv_a;
         const R zeta = ((pr.zh + sh) + (pr.zl + sl)) * inv_a;
         R xi = R(0), eta = R(0);
-        if constexpr (D >= 2) xi = ((R)(c[1] - S.icf[1]) + (o[1] - R(S.frf[1]))) * (b.dxr * inv_a);
-        if constexpr (D >= 3) eta = ((R)(c[2] - S.icf[2]) + (o[2] - R(S.frf[2]))) * (b.dxr * inv_a);
+        if constexpr (D >= 2) xi = ((R)(c[1] - S.icf[1]) + (o[1] - b.frf[1])) * (b.dxr * inv_a);
+        if constexpr (D >= 3) eta = ((R)(c[2] - S.icf[2]) + (o[2] - b.frf[2])) * (b.dxr * inv_a);
         R Ep[3], Bp[3];
         focused_field<R>(b, xi, eta, zeta, tmz, tpz, pr.trel, Ep, Bp);
         E[0] = Ep[2];

@@ -192,10 +192,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
 
         const BeamC<R>& bc = beam_of<R>(S);
         const PhaseRef<R> pref = s_pref;
-        const R dt = R(S.dt);
-        const R dtdx = R(S.dt * S.inv_dx);
-        const R jfac = R(S.dx / S.dt);              // -q dx/dt, q = -1
-        const R hq = R(-0.5 * S.dt);                // q dt / 2
+        const R dtdx = bc.dtdx;
+        const R jfac = bc.jfac;                     // -q dx/dt, q = -1
+        const R hq = bc.hq;                         // q dt / 2
         const int hx[3] = {4, 2, 2};                // box halo below the tile per axis
 
         // Rounds of 256 particles.  With P particles per cell (1, 2, 4 or 8) sitting next to

@@ -38,6 +38,8 @@ struct BeamC {
     R a0, dur, inv_dur, t_c;                                  // plane wave
     R dxr;                                                    // cell size
     R eu[3], bu[3];
+    // push constants: q dt/2 (q = -1), dt/dx, -q dx/dt, focus offset within its cell per axis
+    R hq, dtdx, jfac, frf[3];
 };
 
 // Field-solver constants in the working precision R, computed on the host at set-up.
