@@ -55,6 +55,11 @@ def parse():
 
 SCALE = 1
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from the
+# ncu capture summarised in profiles/ (kept in step with the kernel: set to None when the
+# kernel changes and until it is captured again)
+PROFILED_TRAFFIC = {("2d_lp_1024sq", "k_push<2,float>"): (75.3e6, "profiles/k_push_2d_lp_1024sq.md, ~step 80")}
+
 
 def workload(name):
     w = {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp}[name]()
@@ -249,9 +254,11 @@ def run_ours(args, rank, world, local_rank):
     es = 4 if w.precision == synth.FP32 else 8
     cells = w.n_cells
     yee_bytes = cells * (9 * es + 6 * es + 3 * es)           # read E, B, J; write E, B; clear J
+    kname = "k_push<%d,%s>" % (w.dim, "float" if es == 4 else "double")
+    traffic = PROFILED_TRAFFIC.get((w.name, kname))
     roof = {"bound": "alu", "achieved": round(fl / push_s / 1e12, 3), "peak": round(fp32_peak, 2),
-            "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": None,
-            "kernel": "k_push<%d,%s>" % (w.dim, "float" if es == 4 else "double"),
+            "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else None, "kernel": kname,
             "peak_source": f"SM count x FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
             "push_ms": round(push_s * 1e3, 4),
             "hbm_view": {"achieved_gbs": round(by / push_s / 1e9, 1), "peak_gbs": hbm, "frac": round(hbm_frac, 4),
