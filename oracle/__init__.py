@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 BEAM_NONE, BEAM_PLANE, BEAM_LP, BEAM_RP, BEAM_UNIFORM = 0, 1, 2, 3, 4
+PUSHER_BORIS, PUSHER_VAY, PUSHER_HC = 0, 1, 2
 ENV_SIN2, ENV_GAUSS = 0, 1
 BC_MUR, BC_PERIODIC = 0, 1
 
@@ -67,6 +68,7 @@ class OrcConfig(ctypes.Structure):
         ("ppc", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("remove_margin", ctypes.c_int),
+        ("pusher", ctypes.c_int),
     ]
 
 
@@ -265,4 +267,4 @@ def config_from(w, field_bc: int = BC_MUR, tf_mode: int = 0) -> OrcConfig:
                        envelope=w.envelope, a0=w.a0, duration=w.duration, phi0=w.phi0, t_focus=w.t_focus,
                        focus=w.focus, a=a, s=s, psi0=psi0, e_unif=w.e_unif, b_unif=w.b_unif,
                        slab_lo=w.slab_lo, slab_hi=w.slab_hi, n_e=w.n_e, ppc=w.ppc, seed=w.seed,
-                       remove_margin=w.remove_margin)
+                       remove_margin=w.remove_margin, pusher=w.pusher)

@@ -789,6 +789,81 @@ static void add_exit(orc_sim* s, const double u[3], double w, int64_t id)
     s->nexit++;
 }
 
+/* ---- momentum updates (h = q dt / 2m, m = 1, c = 1) -------------------------------
+ * All three take u^{n-1/2} and the fields at x^n to u^{n+1/2}.  a x b: cross product. */
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Boris: half electric kick, rotation about B by the angle 2 atan(|h B|/gamma^-), half kick. */
+static void push_boris(double u[3], const double E[3], const double B[3], double h)
+{
+    double um[3], tv[3], sv[3], c1[3], up[3], c2[3];
+    for (int c = 0; c < 3; c++) um[c] = u[c] + h * E[c];
+    const double gm = sqrt(1.0 + dot3(um, um));
+    for (int c = 0; c < 3; c++) tv[c] = h / gm * B[c];
+    const double t2 = dot3(tv, tv);
+    for (int c = 0; c < 3; c++) sv[c] = 2.0 * tv[c] / (1.0 + t2);
+    cross3(um, tv, c1);
+    for (int c = 0; c < 3; c++) up[c] = um[c] + c1[c];
+    cross3(up, sv, c2);
+    for (int c = 0; c < 3; c++) u[c] = um[c] + c2[c] + h * E[c];
+}
+
+/* gamma of the rotation in the Vay and Higuera-Cary schemes: the positive root of
+ * g^4 - sigma g^2 - (tau^2 + (w.tau)^2) = 0, sigma = 1 + w^2 - tau^2, for the vector w the
+ * rotation acts on and tau = h B */
+static double implicit_gamma(const double w[3], const double tau[3])
+{
+    const double t2 = dot3(tau, tau), ws = dot3(w, tau);
+    const double sigma = 1.0 + dot3(w, w) - t2;
+    return sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (t2 + ws * ws))));
+}
+
+/* the solution v of v - v x t = w (implicit midpoint rotation): s (w + (w.t) t + w x t),
+ * s = 1/(1 + t^2) */
+static void midpoint_rotation(const double w[3], const double t[3], double v[3])
+{
+    double c[3];
+    cross3(w, t, c);
+    const double wt = dot3(w, t), s = 1.0 / (1.0 + dot3(t, t));
+    for (int k = 0; k < 3; k++) v[k] = s * (w[k] + wt * t[k] + c[k]);
+}
+
+/* Vay (2008): a full kick of E + v x B with the old velocity to the half step, a second
+ * electric half kick, then u^{n+1/2} from the implicit midpoint rotation with the gamma of
+ * the new momentum. */
+static void push_vay(double u[3], const double E[3], const double B[3], double h)
+{
+    const double g0 = sqrt(1.0 + dot3(u, u));
+    double v[3], vxb[3], w[3], tau[3], t[3];
+    for (int c = 0; c < 3; c++) v[c] = u[c] / g0;
+    cross3(v, B, vxb);
+    for (int c = 0; c < 3; c++) w[c] = u[c] + h * (E[c] + vxb[c]) + h * E[c];
+    for (int c = 0; c < 3; c++) tau[c] = h * B[c];
+    const double g1 = implicit_gamma(w, tau);
+    for (int c = 0; c < 3; c++) t[c] = tau[c] / g1;
+    midpoint_rotation(w, t, u);
+}
+
+/* Higuera-Cary (2017): electric half kick to u^-, the implicit midpoint rotation with the
+ * gamma of the mid-rotation momentum ubar (u^+ = 2 ubar - u^-), electric half kick. */
+static void push_higuera_cary(double u[3], const double E[3], const double B[3], double h)
+{
+    double um[3], tau[3], t[3], ub[3];
+    for (int c = 0; c < 3; c++) um[c] = u[c] + h * E[c];
+    for (int c = 0; c < 3; c++) tau[c] = h * B[c];
+    const double gb = implicit_gamma(um, tau);
+    for (int c = 0; c < 3; c++) t[c] = tau[c] / gb;
+    midpoint_rotation(um, t, ub);
+    for (int c = 0; c < 3; c++) u[c] = 2.0 * ub[c] - um[c] + h * E[c];
+}
+
 void orc_step(orc_sim* s, int nsteps)
 {
     const double dt = s->c.dt, dx = s->c.dx;
@@ -809,21 +884,11 @@ void orc_step(orc_sim* s, int nsteps)
                 orc_incident(&s->c, x, t, Ei, Bi);
                 for (int c = 0; c < 3; c++) { E[c] += Ei[c]; B[c] += Bi[c]; }
             }
-            /* relativistic Boris rotation (charge q, mass 1) */
-            double h = 0.5 * q * dt;
-            double um[3], tv[3], sv[3], up[3], upp[3];
-            for (int c = 0; c < 3; c++) um[c] = u[c] + h * E[c];
-            double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-            for (int c = 0; c < 3; c++) tv[c] = h / gm * B[c];
-            double t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-            for (int c = 0; c < 3; c++) sv[c] = 2.0 * tv[c] / (1.0 + t2);
-            up[0] = um[0] + (um[1] * tv[2] - um[2] * tv[1]);
-            up[1] = um[1] + (um[2] * tv[0] - um[0] * tv[2]);
-            up[2] = um[2] + (um[0] * tv[1] - um[1] * tv[0]);
-            upp[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]);
-            upp[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]);
-            upp[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]);
-            for (int c = 0; c < 3; c++) u[c] = upp[c] + h * E[c];
+            /* momentum update of the Lorentz force (charge q, mass 1) */
+            const double h = 0.5 * q * dt;
+            if (s->c.pusher == ORC_PUSHER_VAY) push_vay(u, E, B, h);
+            else if (s->c.pusher == ORC_PUSHER_HC) push_higuera_cary(u, E, B, h);
+            else push_boris(u, E, B, h);
             double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             double v[3] = {u[0] / g, u[1] / g, u[2] / g};
             double xn[3] = {x[0], x[1], x[2]};

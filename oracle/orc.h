@@ -25,6 +25,9 @@ extern "C" {
 #endif
 
 enum { ORC_BEAM_NONE = 0, ORC_BEAM_PLANE = 1, ORC_BEAM_LP = 2, ORC_BEAM_RP = 3, ORC_BEAM_UNIFORM = 4 };
+/* Boris (1970); Vay, Phys. Plasmas 15, 056701 (2008); Higuera & Cary, Phys. Plasmas 24,
+ * 052104 (2017) */
+enum { ORC_PUSHER_BORIS = 0, ORC_PUSHER_VAY = 1, ORC_PUSHER_HC = 2 };
 enum { ORC_ENV_SIN2 = 0, ORC_ENV_GAUSS = 1 };
 enum { ORC_BC_MUR = 0, ORC_BC_PERIODIC = 1 };
 
@@ -49,6 +52,7 @@ typedef struct {
     int ppc;              /* particles per cell */
     uint64_t seed;        /* SplitMix64 seed */
     int remove_margin;    /* open boxes: a particle whose position is closer than this many cells to a face is removed */
+    int pusher;           /* ORC_PUSHER_*: the momentum update of the Lorentz force (Sec. 2 cites all three) */
 } orc_config;
 
 typedef struct orc_sim orc_sim;

@@ -57,6 +57,7 @@ class Workload:
     e_unif: tuple = (0.0, 0.0, 0.0)
     b_unif: tuple = (0.0, 0.0, 0.0)
     remove_margin: int = 3
+    pusher: int = 0                      # 0 Boris, 1 Vay, 2 Higuera-Cary
 
     @property
     def dt(self) -> float:
