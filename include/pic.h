@@ -63,6 +63,11 @@ enum { PIC_ENV_SIN2 = 0, PIC_ENV_GAUSS = 1 };
  * the particle coordinate it needs are formed in double precision first. */
 enum { PIC_FP64 = 0, PIC_FP32 = 1 };
 
+/* Momentum update: Boris (1970); Vay, Phys. Plasmas 15, 056701 (2008), which keeps the
+ * force-free E x B drift of relativistic particles; Higuera & Cary, Phys. Plasmas 24,
+ * 052104 (2017), which keeps it and is volume preserving. */
+enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1, PIC_PUSHER_HC = 2 };
+
 /* device status word bits (pic_info.status) */
 enum {
     PIC_FLAG_TIMEOUT = 1u << 0,      /* an mbarrier wait exceeded its iteration bound */
@@ -101,6 +106,7 @@ typedef struct {
     int64_t max_particles;   /* particle capacity; 0: slab count (pic_set_particles may need more) */
     int64_t max_exits;       /* exit-record capacity; 0: max_particles */
     int32_t chunk;           /* particles per push work item (multiple of 256, 256..16384); 0: default */
+    int32_t pusher;          /* PIC_PUSHER_*: momentum update of the Lorentz force (Sec. 2 cites all three) */
     int32_t autotune_steps;  /* > 0: pic_init first runs pic_autotune with this many trial steps
                                 for a tile or chunk left at 0 (cached per shape) */
 } pic_config;

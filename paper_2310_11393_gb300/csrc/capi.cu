@@ -196,6 +196,8 @@ pic_status validate(const pic_config* c, pic_sim* s)
     if (c->chunk < 0 || (c->chunk > 0 && (c->chunk % 256 || c->chunk > 16384)))
         return fail(s, PIC_EINVAL, "chunk = %d invalid (a multiple of 256, <= 16384)", c->chunk);
     if (c->autotune_steps < 0) return fail(s, PIC_EINVAL, "autotune_steps must be >= 0");
+    if (c->pusher < PIC_PUSHER_BORIS || c->pusher > PIC_PUSHER_HC)
+        return fail(s, PIC_EINVAL, "unknown pusher %d", c->pusher);
     int bits = 0;
     for (int d = 0; d < c->dim; ++d) bits += bits_for(c->n[d]);
     if (bits > 31) return fail(s, PIC_EINVAL, "grid too large for the packed cell index");
@@ -583,6 +585,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.nptiles = L.nptiles;
     h.nytiles = L.nytiles;
     h.margin = cfg->remove_margin > 0 ? cfg->remove_margin : 3;
+    h.pusher = cfg->pusher;
     h.dx = cfg->dx;
     h.dt = prm.dt;
     h.inv_dx = 1.0 / cfg->dx;

@@ -123,6 +123,77 @@ __device__ __forceinline__ ChunkRef chunk_of(const SimDev* __restrict__ sims, in
     return r;
 }
 
+// ---- momentum updates; h = q dt / 2 (q = -1, m = 1, c = 1) ----------------------------
+
+// Boris: electric half kick, rotation about B by 2 atan(|h B|/gamma^-), electric half kick.
+template <typename R>
+__device__ __forceinline__ void boris_update(R u[3], const R E[3], const R B[3], R h)
+{
+    R um[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
+    const R gm = m_sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const R tf = h / gm;
+    const R tv[3] = {tf * B[0], tf * B[1], tf * B[2]};
+    const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+    const R sf = R(2) / (R(1) + t2);
+    const R up[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]), um[1] + (um[2] * tv[0] - um[0] * tv[2]),
+                     um[2] + (um[0] * tv[1] - um[1] * tv[0])};
+    const R sv[3] = {sf * tv[0], sf * tv[1], sf * tv[2]};
+    u[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + h * E[0];
+    u[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + h * E[1];
+    u[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + h * E[2];
+}
+
+// Implicit-midpoint rotation shared by the Vay and Higuera-Cary schemes: with tau = h B,
+// gamma^2 is the positive root of g^4 - sigma g^2 - (tau^2 + (w.tau)^2) = 0,
+// sigma = 1 + w^2 - tau^2 (taken in the form without cancellation for either sign of
+// sigma), t = tau/gamma and the result solves v - v x t = w: v = (w + (w.t) t + w x t)/(1 + t^2).
+template <typename R>
+__device__ __forceinline__ void midpoint_rotation(const R w[3], const R B[3], R h, R v[3])
+{
+    const R tau[3] = {h * B[0], h * B[1], h * B[2]};
+    const R t2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    const R ws = w[0] * tau[0] + w[1] * tau[1] + w[2] * tau[2];
+    const R sigma = R(1) + w[0] * w[0] + w[1] * w[1] + w[2] * w[2] - t2;
+    const R K = t2 + ws * ws;
+    const R Dq = m_sqrt(sigma * sigma + R(4) * K);
+    const R g2 = sigma >= R(0) ? R(0.5) * (sigma + Dq) : R(2) * K / (Dq - sigma);
+    const R ig = R(1) / m_sqrt(g2);
+    const R t[3] = {tau[0] * ig, tau[1] * ig, tau[2] * ig};
+    const R tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const R wt = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
+    const R sf = R(1) / (R(1) + tt);
+    v[0] = sf * (w[0] + wt * t[0] + (w[1] * t[2] - w[2] * t[1]));
+    v[1] = sf * (w[1] + wt * t[1] + (w[2] * t[0] - w[0] * t[2]));
+    v[2] = sf * (w[2] + wt * t[2] + (w[0] * t[1] - w[1] * t[0]));
+}
+
+// Vay (2008): kick by E + v x B with the old velocity, a second electric half kick, then the
+// implicit-midpoint rotation with the gamma of the new momentum.
+template <typename R>
+__device__ __forceinline__ void vay_update(R u[3], const R E[3], const R B[3], R h)
+{
+    const R ig0 = R(1) / m_sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R v[3] = {u[0] * ig0, u[1] * ig0, u[2] * ig0};
+    const R w[3] = {u[0] + h * (R(2) * E[0] + (v[1] * B[2] - v[2] * B[1])),
+                    u[1] + h * (R(2) * E[1] + (v[2] * B[0] - v[0] * B[2])),
+                    u[2] + h * (R(2) * E[2] + (v[0] * B[1] - v[1] * B[0]))};
+    midpoint_rotation<R>(w, B, h, u);
+}
+
+// Higuera-Cary (2017): electric half kick to u^-, implicit-midpoint rotation to the
+// mid-rotation momentum ubar (gamma of ubar), u^+ = 2 ubar - u^-, electric half kick.
+template <typename R>
+__device__ __forceinline__ void higuera_cary_update(R u[3], const R E[3], const R B[3], R h)
+{
+    const R um[3] = {u[0] + h * E[0], u[1] + h * E[1], u[2] + h * E[2]};
+    R ub[3];
+    midpoint_rotation<R>(um, B, h, ub);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = R(2) * ub[d] - um[d] + h * E[d];
+}
+
 template <int D, typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_push(const SimDev* __restrict__ sims, int nsims,
                                               const int* __restrict__ gprefix, int* __restrict__ counter)
@@ -253,21 +324,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
                 }
             }
 
-            // ---- relativistic Boris push, charge -1, mass 1 ----
-            R um[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) um[d] = u[d] + hq * E[d];
-            const R gm = m_sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-            const R tf = hq / gm;
-            const R tv[3] = {tf * B[0], tf * B[1], tf * B[2]};
-            const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-            const R sf = R(2) / (R(1) + t2);
-            const R up[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]), um[1] + (um[2] * tv[0] - um[0] * tv[2]),
-                             um[2] + (um[0] * tv[1] - um[1] * tv[0])};
-            const R sv[3] = {sf * tv[0], sf * tv[1], sf * tv[2]};
-            u[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + hq * E[0];
-            u[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + hq * E[1];
-            u[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + hq * E[2];
+            // ---- momentum update, charge -1, mass 1 (u^{n-1/2} -> u^{n+1/2}) ----
+            if (S.pusher == 1) vay_update<R>(u, E, B, hq);
+            else if (S.pusher == 2) higuera_cary_update<R>(u, E, B, hq);
+            else boris_update<R>(u, E, B, hq);
             const R ig = R(1) / m_sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             const R v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
 

@@ -72,7 +72,7 @@ struct alignas(128) SimDev {
     int yb[3];                // field-solver box extent per axis
     int cb[3];                // bits of each cell coordinate in the packed cell index
     int margin;
-    int pad0;
+    int pusher;               // 0 Boris, 1 Vay, 2 Higuera-Cary
     double dx, dt, inv_dx;
     // incident field
     double a0, duration, phi0, t_focus, a, s, psi0;

@@ -33,7 +33,7 @@ class pic_config(Structure):
         ("focus", c_double * 3), ("a_param", c_double), ("s_param", c_double), ("psi0", c_double),
         ("e_unif", c_double * 3), ("b_unif", c_double * 3), ("slab_lo", c_int32 * 3), ("slab_hi", c_int32 * 3),
         ("n_e", c_double), ("ppc", c_int32), ("tile", c_int32 * 3), ("seed", c_uint64),
-        ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("autotune_steps", c_int32),
+        ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("pusher", c_int32), ("autotune_steps", c_int32),
     ]
 
 
@@ -128,6 +128,9 @@ def load():
     L.pic_serve_close.argtypes = [P]
     _lib = L
     return L
+
+
+PIC_PUSHER_BORIS, PIC_PUSHER_VAY, PIC_PUSHER_HC = 0, 1, 2
 
 
 class PicError(RuntimeError):
@@ -329,6 +332,7 @@ def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chun
     c.max_exits = max_exits
     c.chunk = chunk
     c.autotune_steps = autotune_steps
+    c.pusher = getattr(w, "pusher", 0)
     return c
 
 
