@@ -23,8 +23,9 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-BEAM_NONE, BEAM_PLANE, BEAM_LP, BEAM_RP, BEAM_UNIFORM = 0, 1, 2, 3, 4
+BEAM_NONE, BEAM_PLANE, BEAM_LP, BEAM_RP, BEAM_UNIFORM, BEAM_GAUSS2D = 0, 1, 2, 3, 4, 5
 PUSHER_BORIS, PUSHER_VAY, PUSHER_HC = 0, 1, 2
+PROFILE_UNIFORM, PROFILE_SUPERGAUSS = 0, 1
 ENV_SIN2, ENV_GAUSS = 0, 1
 BC_MUR, BC_PERIODIC = 0, 1
 
@@ -69,6 +70,12 @@ class OrcConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("remove_margin", ctypes.c_int),
         ("pusher", ctypes.c_int),
+        ("w0", ctypes.c_double),
+        ("profile", ctypes.c_int),
+        ("prof_order", ctypes.c_int),
+        ("prof_x0", ctypes.c_double),
+        ("prof_fwhm", ctypes.c_double),
+        ("prof_cut", ctypes.c_double),
     ]
 
 
@@ -267,4 +274,5 @@ def config_from(w, field_bc: int = BC_MUR, tf_mode: int = 0) -> OrcConfig:
                        envelope=w.envelope, a0=w.a0, duration=w.duration, phi0=w.phi0, t_focus=w.t_focus,
                        focus=w.focus, a=a, s=s, psi0=psi0, e_unif=w.e_unif, b_unif=w.b_unif,
                        slab_lo=w.slab_lo, slab_hi=w.slab_hi, n_e=w.n_e, ppc=w.ppc, seed=w.seed,
-                       remove_margin=w.remove_margin, pusher=w.pusher)
+                       remove_margin=w.remove_margin, pusher=w.pusher, w0=w.w0, profile=w.profile,
+                       prof_order=w.prof_order, prof_x0=w.prof_x0, prof_fwhm=w.prof_fwhm, prof_cut=w.prof_cut)

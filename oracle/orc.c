@@ -231,6 +231,34 @@ static double plane_wave(const orc_config* c, double x, double t)
     return c->a0 * sin(xi - xic + c->phi0) * env;
 }
 
+/* 2D paraxial Gaussian beam of Sec. 3.2, Eq. (gauss2D), focus at the origin of (X, Z),
+ * propagation +Z, polarisation X (the paper's x, z), k = omega = 1:
+ *   w(Z) = w0 sqrt(1 + (Z/zR)^2), zR = w0^2/2, 1/R(Z) = Z/(Z^2 + zR^2), eta = atan(Z/zR)/2,
+ *   E_x = E0 sqrt(w0/w) exp(-X^2/w^2) cos(Z - t + X^2/(2R) - eta + phi0) env,  B_y = E_x,
+ *   E_z = E0 sqrt(w0/w) exp(-X^2/w^2) [2 (X/w^2) sin(same phase) - (X/R) cos(same phase)] env,
+ *   env = 2^{-4 (t - t0 - Z)^2 / FWHM_T^2}.
+ * E_z is the longitudinal field to first order in 1/(k w0), the one that makes div E vanish
+ * to that order at every Z (E_z = Re[i dA/dX e^{i(Z-t)}] for E_x = Re[A e^{i(Z-t)}]).  At
+ * the focus (1/R = 0) it is the printed form, with the printed factor X/w(Z) read as
+ * X/w(Z)^2; the printed form omits the curvature term -(X/R) cos, of the same order. */
+static void gauss2d_field(const orc_config* c, double Z, double X, double t, double Ep[3], double Bp[3])
+{
+    const double w0 = c->w0, zR = 0.5 * w0 * w0;
+    const double w = w0 * sqrt(1.0 + (Z / zR) * (Z / zR));
+    const double invR = Z / (Z * Z + zR * zR);
+    const double eta = 0.5 * atan(Z / zR);
+    const double xi = t - c->t_focus - Z;
+    const double env = pow(2.0, -4.0 * xi * xi / (c->duration * c->duration));
+    const double amp = c->a0 * sqrt(w0 / w) * exp(-X * X / (w * w)) * env;
+    const double ph = Z - t + 0.5 * X * X * invR - eta + c->phi0;
+    Ep[0] = amp * cos(ph);
+    Ep[1] = 0.0;
+    Ep[2] = amp * (2.0 * X / (w * w) * sin(ph) - X * invR * cos(ph));
+    Bp[0] = 0.0;
+    Bp[1] = Ep[0];
+    Bp[2] = 0.0;
+}
+
 void orc_incident(const orc_config* c, const double x[3], double t, double E[3], double B[3])
 {
     for (int d = 0; d < 3; d++) { E[d] = 0; B[d] = 0; }
@@ -256,6 +284,14 @@ void orc_incident(const orc_config* c, const double x[3], double t, double E[3],
     case ORC_BEAM_UNIFORM:
         for (int d = 0; d < 3; d++) { E[d] = c->e_unif[d]; B[d] = c->b_unif[d]; }
         break;
+    case ORC_BEAM_GAUSS2D: {
+        /* same frame as the 2D slice of LP/RP: paper z = grid x, paper x = grid y */
+        double Ep[3], Bp[3];
+        gauss2d_field(c, x[0] - c->focus[0], (c->dim >= 2) ? x[1] - c->focus[1] : 0.0, t, Ep, Bp);
+        E[0] = Ep[2]; E[1] = Ep[0]; E[2] = Ep[1];
+        B[0] = Bp[2]; B[1] = Bp[0]; B[2] = Bp[1];
+        break;
+    }
     default:
         break;
     }
@@ -446,6 +482,15 @@ void orc_charge_density(const orc_sim* s, double* out)
     }
 }
 
+/* density profile along x at position x (code units): Sec. 3.1's super-Gaussian
+ * n(x)/n0 = 2^-[2 (x - x0)/FWHM]^p beyond the cut (0 before it), or 1 */
+static double profile_factor(const orc_config* c, double x)
+{
+    if (c->profile != ORC_PROFILE_SUPERGAUSS) return 1.0;
+    if (x <= c->prof_cut) return 0.0;
+    return pow(2.0, -pow(2.0 * (x - c->prof_x0) / c->prof_fwhm, (double)c->prof_order));
+}
+
 orc_sim* orc_create(const orc_config* cfg)
 {
     orc_sim* s = calloc(1, sizeof(orc_sim));
@@ -488,7 +533,7 @@ orc_sim* orc_create(const orc_config* cfg)
                         }
                         s->pu[3 * p + d] = 0.0;
                     }
-                    s->pw[p] = cfg->n_e / cfg->ppc;
+                    s->pw[p] = cfg->n_e / cfg->ppc * profile_factor(cfg, s->px[3 * p]);
                     s->pid[p] = p;
                 }
     s->np = np;

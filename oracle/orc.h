@@ -24,7 +24,10 @@
 extern "C" {
 #endif
 
-enum { ORC_BEAM_NONE = 0, ORC_BEAM_PLANE = 1, ORC_BEAM_LP = 2, ORC_BEAM_RP = 3, ORC_BEAM_UNIFORM = 4 };
+enum { ORC_BEAM_NONE = 0, ORC_BEAM_PLANE = 1, ORC_BEAM_LP = 2, ORC_BEAM_RP = 3, ORC_BEAM_UNIFORM = 4,
+       ORC_BEAM_GAUSS2D = 5 };
+/* slab density profile along x: uniform, or the super-Gaussian of Sec. 3.1 */
+enum { ORC_PROFILE_UNIFORM = 0, ORC_PROFILE_SUPERGAUSS = 1 };
 /* Boris (1970); Vay, Phys. Plasmas 15, 056701 (2008); Higuera & Cary, Phys. Plasmas 24,
  * 052104 (2017) */
 enum { ORC_PUSHER_BORIS = 0, ORC_PUSHER_VAY = 1, ORC_PUSHER_HC = 2 };
@@ -53,6 +56,12 @@ typedef struct {
     uint64_t seed;        /* SplitMix64 seed */
     int remove_margin;    /* open boxes: a particle whose position is closer than this many cells to a face is removed */
     int pusher;           /* ORC_PUSHER_*: the momentum update of the Lorentz force (Sec. 2 cites all three) */
+    double w0;            /* ORC_BEAM_GAUSS2D waist (a0 = E0, duration = FWHM_T, t_focus = t0, focus) */
+    int profile;          /* ORC_PROFILE_*: electron weight n_e f(x)/ppc at the particle's initial x */
+    int prof_order;       /* super-Gaussian order p */
+    double prof_x0;       /* f(x) = 0 for x <= prof_cut, else 2^-[2 (x - prof_x0)/prof_fwhm]^p */
+    double prof_fwhm;
+    double prof_cut;
 } orc_config;
 
 typedef struct orc_sim orc_sim;

@@ -19,7 +19,8 @@ LAMBDA_UM = 0.8                                  # central wavelength of the pre
 T_R_FS = LAMBDA_UM * 1e-6 / (2 * math.pi * 299792458.0) * 1e15   # 1/omega in fs
 TWO_PI = 2.0 * math.pi
 
-BEAM_NONE, BEAM_PLANE, BEAM_LP, BEAM_RP, BEAM_UNIFORM = 0, 1, 2, 3, 4
+BEAM_NONE, BEAM_PLANE, BEAM_LP, BEAM_RP, BEAM_UNIFORM, BEAM_GAUSS2D = 0, 1, 2, 3, 4, 5
+PROFILE_UNIFORM, PROFILE_SUPERGAUSS = 0, 1
 ENV_SIN2, ENV_GAUSS = 0, 1
 FP64, FP32 = 0, 1
 
@@ -58,6 +59,11 @@ class Workload:
     b_unif: tuple = (0.0, 0.0, 0.0)
     remove_margin: int = 3
     pusher: int = 0                      # 0 Boris, 1 Vay, 2 Higuera-Cary
+    profile: int = PROFILE_UNIFORM       # slab density along x: uniform or super-Gaussian (Sec. 3.1)
+    prof_order: int = 12
+    prof_x0: float = 0.0
+    prof_fwhm: float = 1.0
+    prof_cut: float = 0.0
 
     @property
     def dt(self) -> float:
