@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (default: the workload's full run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "batch", "serve"])
+    ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "2d_gauss", "batch", "serve"])
     ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
     ap.add_argument("--autotune", type=int, default=10,
                     help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
@@ -62,7 +62,7 @@ PROFILED_TRAFFIC = {("2d_lp_1024sq", "k_push<2,float>"): (75.3e6, "profiles/k_pu
 
 
 def workload(name):
-    w = {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp}[name]()
+    w = {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp, "2d_gauss": synth.c6_2d_gauss}[name]()
     return w if SCALE == 1 else synth.scaled(w, SCALE)
 
 
@@ -138,8 +138,10 @@ def flops_per_push(w):
     D = w.dim
     gather = {1: 6 * 6 + 12, 2: 6 * 24 + 24, 3: 6 * 78 + 36}[D]
     boris = 60
-    deposit = {1: 40, 2: 350, 3: 1700}[D]
-    incident = {synth.BEAM_LP: 280, synth.BEAM_RP: 270, synth.BEAM_PLANE: 25}.get(w.beam, 0)
+    # Esirkepov on four-node windows: per axis two order-2 shapes; along the current's own axis
+    # three partial sums per transverse node, 2D Jz / 3D every component over 4^(D-1) nodes
+    deposit = {1: 40, 2: 300, 3: 970}[D]
+    incident = {synth.BEAM_LP: 280, synth.BEAM_RP: 270, synth.BEAM_PLANE: 25, synth.BEAM_GAUSS2D: 45}.get(w.beam, 0)
     move = 5 * D
     return gather + boris + deposit + incident + move
 
@@ -276,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if es == 4 else "f64", "data": "synthetic",
            "config": {"workload": w.name, "dim": w.dim, "grid": list(w.n[: w.dim]), "particles": w.n_particles,
-                      "ppc": w.ppc, "beam": {1: "plane", 2: "LP", 3: "RP"}[w.beam],
+                      "ppc": w.ppc, "beam": {1: "plane", 2: "LP", 3: "RP", 5: "Gaussian 2D"}[w.beam],
                       "precision": "fp32 body, fp64 phase" if es == 4 else "fp64",
                       "cell_updates_per_s": cells * args.steps * world / t_max,
                       "l2": "inputs larger than L2 (device state %.2f GB > 129 MB)" % (info.params.device_bytes / 1e9),

@@ -55,7 +55,15 @@ typedef enum {
     PIC_ENOTFOUND = -9    /* unknown ticket / handle */
 } pic_status;
 
-enum { PIC_BEAM_NONE = 0, PIC_BEAM_PLANE = 1, PIC_BEAM_LP = 2, PIC_BEAM_RP = 3, PIC_BEAM_UNIFORM = 4 };
+/* PIC_BEAM_GAUSS2D: the 2D paraxial Gaussian beam of Sec. 3.2, Eq. (gauss2D) (dim 2 only):
+ * waist w0, amplitude a0 = E0, FWHM_T = duration, envelope centre crossing the focus at
+ * t_focus, carrier cos(Z - t + X^2/(2R) - eta + phi0); longitudinal field to first order in
+ * 1/(k w0) including the wavefront-curvature term. */
+enum { PIC_BEAM_NONE = 0, PIC_BEAM_PLANE = 1, PIC_BEAM_LP = 2, PIC_BEAM_RP = 3, PIC_BEAM_UNIFORM = 4,
+       PIC_BEAM_GAUSS2D = 5 };
+/* Slab density along x: uniform, or Sec. 3.1's super-Gaussian n0 2^-[2 (x - x0)/FWHM]^p beyond
+ * a cut (0 before it); each electron's weight is n_e f(x)/ppc at its initial position. */
+enum { PIC_PROFILE_UNIFORM = 0, PIC_PROFILE_SUPERGAUSS = 1 };
 enum { PIC_ENV_SIN2 = 0, PIC_ENV_GAUSS = 1 };
 /* PIC_FP64: every quantity in double precision.
  * PIC_FP32: particles, fields and the incident-field body in single precision; the
@@ -107,6 +115,10 @@ typedef struct {
     int64_t max_exits;       /* exit-record capacity; 0: max_particles */
     int32_t chunk;           /* particles per push work item (multiple of 256, 256..16384); 0: default */
     int32_t pusher;          /* PIC_PUSHER_*: momentum update of the Lorentz force (Sec. 2 cites all three) */
+    int32_t profile;         /* PIC_PROFILE_*; the super-Gaussian uses prof_order (p >= 1), prof_x0,
+                                prof_fwhm (> 0) and prof_cut, all in code units along x */
+    int32_t prof_order;
+    double prof_x0, prof_fwhm, prof_cut;
     int32_t autotune_steps;  /* > 0: pic_init first runs pic_autotune with this many trial steps
                                 for a tile or chunk left at 0 (cached per shape) */
 } pic_config;

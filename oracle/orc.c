@@ -483,12 +483,13 @@ void orc_charge_density(const orc_sim* s, double* out)
 }
 
 /* density profile along x at position x (code units): Sec. 3.1's super-Gaussian
- * n(x)/n0 = 2^-[2 (x - x0)/FWHM]^p beyond the cut (0 before it), or 1 */
+ * n(x)/n0 = 2^-|2 (x - x0)/FWHM|^p beyond the cut (0 before it), or 1 (the paper's p = 12 is
+ * even; the modulus keeps odd orders meaningful) */
 static double profile_factor(const orc_config* c, double x)
 {
     if (c->profile != ORC_PROFILE_SUPERGAUSS) return 1.0;
     if (x <= c->prof_cut) return 0.0;
-    return pow(2.0, -pow(2.0 * (x - c->prof_x0) / c->prof_fwhm, (double)c->prof_order));
+    return pow(2.0, -pow(fabs(2.0 * (x - c->prof_x0) / c->prof_fwhm), (double)c->prof_order));
 }
 
 orc_sim* orc_create(const orc_config* cfg)

@@ -57,6 +57,10 @@ inline BeamC<R> make_beam_consts(const SimDev& S)
         b.bu[d] = R(S.b_unif[d]);
         b.frf[d] = R(S.frf[d]);
     }
+    b.gw0 = R(S.w0);
+    b.ginv_zr = R(S.w0 > 0 ? 2.0 / (S.w0 * S.w0) : 0.0);
+    b.ginv_w02 = R(S.w0 > 0 ? 1.0 / (S.w0 * S.w0) : 0.0);
+    b.cph = R(std::remainder(S.phi0 - S.t_focus, 6.283185307179586));
     b.hq = R(-0.5 * S.dt);
     b.dtdx = R(S.dt * S.inv_dx);
     b.jfac = R(S.dx / S.dt);
@@ -335,6 +339,31 @@ __device__ __forceinline__ void incident_at(const SimDev& S, const BeamC<R>& b, 
         B[0] = Bp[2];
         B[1] = Bp[0];
         B[2] = Bp[1];
+    } else if (b.beam == BEAM_GAUSS2D) {
+        // 2D paraxial Gaussian beam (Sec. 3.2), beam frame Z = grid x - focus, X = grid y - focus:
+        // the envelope argument t - t0 - Z and the carrier Z - t = -(t - t0 - Z) - t0 come
+        // from the tile's float-float phase reference
+        const R lx = R(c[0] - pr.x0);
+        const R sh = lx * pr.dxh;
+        const R sl = o[0] * pr.dxr + lx * pr.dxl;
+        const R xi = ((pr.ah - sh) + pr.al) - sl;                 // t - t0 - Z
+        const R ev = R(4) * xi * xi * b.inv_dur * b.inv_dur;
+        if (ev > R(40)) return;                                   // envelope below 2^-40
+        const R Z = (pr.zh + sh) + (pr.zl + sl);
+        R X = R(0);
+        if constexpr (D >= 2) X = ((R)(c[1] - S.icf[1]) + (o[1] - b.frf[1])) * b.dxr;
+        const R zz = Z * b.ginv_zr;
+        const R q1 = R(1) + zz * zz;                              // (w/w0)^2
+        const R iw2 = b.ginv_w02 / q1;                            // 1/w^2
+        const R invR = zz * b.ginv_zr / q1;                       // Z/(Z^2 + zR^2)
+        const R eta = R(0.5) * m_atan(zz);
+        const R amp = b.a0 * m_rsqrt(m_sqrt(q1)) * m_exp(-X * X * iw2) * m_exp2(-ev);
+        const R ph = (b.cph - xi) + (R(0.5) * X * X * invR - eta);
+        R sn, cs;
+        sincos_phase(ph, &sn, &cs);
+        E[1] = amp * cs;                                          // paper E_x
+        B[2] = E[1];                                              // paper B_y
+        E[0] = amp * (R(2) * X * iw2 * sn - X * invR * cs);       // paper E_z
     } else if (b.beam == BEAM_UNIFORM) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {

@@ -168,7 +168,16 @@ pic_status validate(const pic_config* c, pic_sim* s)
             return fail(s, PIC_EINVAL, "n[%d] = %d outside [16, 2^20]", d, c->n[d]);
     if (!(c->dx > 0)) return fail(s, PIC_EINVAL, "dx must be > 0");
     if (c->precision != PIC_FP64 && c->precision != PIC_FP32) return fail(s, PIC_EINVAL, "unknown precision");
-    if (c->beam < PIC_BEAM_NONE || c->beam > PIC_BEAM_UNIFORM) return fail(s, PIC_EINVAL, "unknown beam %d", c->beam);
+    if (c->beam < PIC_BEAM_NONE || c->beam > PIC_BEAM_GAUSS2D) return fail(s, PIC_EINVAL, "unknown beam %d", c->beam);
+    if (c->beam == PIC_BEAM_GAUSS2D) {
+        if (c->dim != 2) return fail(s, PIC_EINVAL, "the 2D Gaussian beam needs dim == 2");
+        if (!(c->w0 > 0) || !(c->duration > 0))
+            return fail(s, PIC_EINVAL, "the 2D Gaussian beam needs w0 > 0 and duration > 0");
+    }
+    if (c->profile < PIC_PROFILE_UNIFORM || c->profile > PIC_PROFILE_SUPERGAUSS)
+        return fail(s, PIC_EINVAL, "unknown profile %d", c->profile);
+    if (c->profile == PIC_PROFILE_SUPERGAUSS && (!(c->prof_fwhm > 0) || c->prof_order < 1 || c->prof_order > 64))
+        return fail(s, PIC_EINVAL, "super-Gaussian profile needs prof_fwhm > 0 and 1 <= prof_order <= 64");
     if ((c->beam == PIC_BEAM_LP || c->beam == PIC_BEAM_RP)) {
         if (c->dim < 2) return fail(s, PIC_EINVAL, "LP/RP beams need dim >= 2");
         if (!(c->a_param > 0 || c->w0 > 0)) return fail(s, PIC_EINVAL, "LP/RP beams need w0 > 0 or a_param > 0");
@@ -590,6 +599,12 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.dt = prm.dt;
     h.inv_dx = 1.0 / cfg->dx;
     h.a0 = cfg->a0;
+    h.w0 = cfg->w0;
+    h.profile = cfg->profile;
+    h.prof_order = cfg->prof_order;
+    h.prof_x0 = cfg->prof_x0;
+    h.prof_fwhm = cfg->prof_fwhm;
+    h.prof_cut = cfg->prof_cut;
     h.duration = cfg->duration;
     h.phi0 = cfg->phi0;
     h.t_focus = cfg->t_focus;

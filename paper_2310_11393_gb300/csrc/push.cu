@@ -736,16 +736,22 @@ __global__ void k_gen_slab(const SimDev* __restrict__ sim, long long n, int ppc,
         const int lo[3] = {lo0, lo1, lo2};
         const long long rel[3] = {cellp % n0, (cellp / n0) % n1, cellp / ((long long)n0 * n1)};
         int c[3] = {0, 0, 0};
+        double x0 = 0.0;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             c[d] = lo[d] + (int)rel[d];
             const unsigned long long r = splitmix64(seed, 3ull * (unsigned long long)p + d);
             const double offd = (double)(r >> 40) * (1.0 / 16777216.0);
             reinterpret_cast<R*>(S.off[1][d])[p] = R(offd);
+            if (d == 0) x0 = ((double)c[0] + offd) * S.dx;
         }
+        // density profile along x (Sec. 3.1's super-Gaussian) at the initial position
+        double f = 1.0;
+        if (S.profile == 1)
+            f = x0 <= S.prof_cut ? 0.0 : exp2(-pow(fabs(2.0 * (x0 - S.prof_x0) / S.prof_fwhm), (double)S.prof_order));
 #pragma unroll
         for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[1][d])[p] = R(0);
-        reinterpret_cast<R*>(S.wgt[1])[p] = R(weight);
+        reinterpret_cast<R*>(S.wgt[1])[p] = R(weight * f);
         S.pid[1][p] = (unsigned)p;
         S.cell[1][p] = encode_cell<D>(S, c);
         atomicAdd(&S.tcnt[tile_of<D>(S, c)], 1);

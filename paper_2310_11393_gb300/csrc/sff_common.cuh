@@ -17,7 +17,7 @@ constexpr int NCOMP = 9;           // Ex Ey Ez Bx By Bz Jx Jy Jz
 constexpr unsigned DEAD = 0xFFFFFFFFu;
 constexpr int EXIT_DOUBLES = 6;    // u[3], w, id, step
 
-enum Beam { BEAM_NONE = 0, BEAM_PLANE = 1, BEAM_LP = 2, BEAM_RP = 3, BEAM_UNIFORM = 4 };
+enum Beam { BEAM_NONE = 0, BEAM_PLANE = 1, BEAM_LP = 2, BEAM_RP = 3, BEAM_UNIFORM = 4, BEAM_GAUSS2D = 5 };
 enum Flag { FLAG_TIMEOUT = 1u, FLAG_CFL = 2u, FLAG_EXIT_OVERFLOW = 4u };
 
 // Device-updated state of one simulation.
@@ -40,6 +40,8 @@ struct BeamC {
     R eu[3], bu[3];
     // push constants: q dt/2 (q = -1), dt/dx, -q dx/dt, focus offset within its cell per axis
     R hq, dtdx, jfac, frf[3];
+    // 2D Gaussian beam: w0, 1/z_R, 1/w0^2, carrier phase offset (phi0 - t_focus) mod 2 pi
+    R gw0, ginv_zr, ginv_w02, cph;
 };
 
 // Field-solver constants in the working precision R, computed on the host at set-up.
@@ -75,7 +77,10 @@ struct alignas(128) SimDev {
     int pusher;               // 0 Boris, 1 Vay, 2 Higuera-Cary
     double dx, dt, inv_dx;
     // incident field
-    double a0, duration, phi0, t_focus, a, s, psi0;
+    double a0, duration, phi0, t_focus, a, s, psi0, w0;
+    // slab density profile (PIC_PROFILE_*)
+    int profile, prof_order;
+    double prof_x0, prof_fwhm, prof_cut;
     double focus[3];
     double e_unif[3], b_unif[3];
     int icf[3];               // focus = (icf + frf) * dx per axis
@@ -348,6 +353,10 @@ __device__ __forceinline__ float m_sin(float x) { return sinf(x); }
 __device__ __forceinline__ double m_sin(double x) { return sin(x); }
 __device__ __forceinline__ float m_sinpi(float x) { return sinpif(x); }
 __device__ __forceinline__ double m_sinpi(double x) { return sinpi(x); }
+__device__ __forceinline__ float m_atan(float x) { return atanf(x); }
+__device__ __forceinline__ double m_atan(double x) { return atan(x); }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_abs(float x) { return fabsf(x); }

@@ -33,7 +33,8 @@ class pic_config(Structure):
         ("focus", c_double * 3), ("a_param", c_double), ("s_param", c_double), ("psi0", c_double),
         ("e_unif", c_double * 3), ("b_unif", c_double * 3), ("slab_lo", c_int32 * 3), ("slab_hi", c_int32 * 3),
         ("n_e", c_double), ("ppc", c_int32), ("tile", c_int32 * 3), ("seed", c_uint64),
-        ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("pusher", c_int32), ("autotune_steps", c_int32),
+        ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("pusher", c_int32), ("profile", c_int32), ("prof_order", c_int32),
+        ("prof_x0", c_double), ("prof_fwhm", c_double), ("prof_cut", c_double), ("autotune_steps", c_int32),
     ]
 
 
@@ -131,6 +132,8 @@ def load():
 
 
 PIC_PUSHER_BORIS, PIC_PUSHER_VAY, PIC_PUSHER_HC = 0, 1, 2
+PIC_BEAM_GAUSS2D = 5
+PIC_PROFILE_UNIFORM, PIC_PROFILE_SUPERGAUSS = 0, 1
 
 
 class PicError(RuntimeError):
@@ -333,6 +336,11 @@ def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chun
     c.chunk = chunk
     c.autotune_steps = autotune_steps
     c.pusher = getattr(w, "pusher", 0)
+    c.profile = getattr(w, "profile", 0)
+    c.prof_order = getattr(w, "prof_order", 12)
+    c.prof_x0 = getattr(w, "prof_x0", 0.0)
+    c.prof_fwhm = getattr(w, "prof_fwhm", 1.0)
+    c.prof_cut = getattr(w, "prof_cut", 0.0)
     return c
 
 

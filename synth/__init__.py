@@ -118,6 +118,25 @@ def c3_3d_rp() -> Workload:
                     n_e=0.01, ppc=4, seed=3, focus=_centred(3, n, dx), t_focus=n[0] * dx / 2.0)
 
 
+def c6_2d_gauss(dx_div: int = 32) -> Workload:
+    """Sec. 3.2's 2D set-up at a cell of lambda/dx_div (the paper runs lambda/16 .. lambda/256):
+    window 2 pi [64, 32] (propagation x, transverse y), paraxial Gaussian beam w0 = 16 lambda,
+    E0 = 4.86, FWHM_T = 2 pi, the envelope peak crossing the focus at t_f = 133 with the focus
+    at x = 133 on the axis y = 32 pi; plasma: the 1D super-Gaussian profile (p = 12) shrunk
+    twofold along x (centre 140.75, FWHM 167.55, nothing before 10 pi), uniform in y, peak
+    0.31 n_c, 4 ppc; CFL 0.95; T_sim = 64 pi."""
+    dx = TWO_PI / dx_div
+    n = (64 * dx_div, 32 * dx_div, 1)
+    x0, F, cut = 281.5 / 2, 335.1 / 2, 10 * math.pi
+    lo = int(math.floor(cut / dx))
+    hi = min(n[0] - 4, int(math.ceil((x0 + 0.65 * F) / dx)))
+    w = Workload(name=f"2d_gauss_sec32_dx{dx_div}", dim=2, n=n, dx=dx, steps=0, beam=BEAM_GAUSS2D, a0=4.86,
+                 duration=TWO_PI, w0=16 * TWO_PI, slab_lo=(lo, 4, 0), slab_hi=(hi, n[1] - 4, 1), n_e=0.31, ppc=4,
+                 seed=6, focus=(133.0, 32 * math.pi, 0.0), t_focus=133.0, profile=PROFILE_SUPERGAUSS,
+                 prof_order=12, prof_x0=x0, prof_fwhm=F, prof_cut=cut)
+    return w.with_(steps=int(round(64 * math.pi / w.dt)))
+
+
 def scaled(w: Workload, factor: int, steps: Optional[int] = None, name: Optional[str] = None) -> Workload:
     """Same physics on a box `factor` times smaller per axis (cell size unchanged):
     slab and focus shrink with the box, the focal time follows the new box."""
