@@ -119,6 +119,10 @@ typedef struct {
                                 prof_fwhm (> 0) and prof_cut, all in code units along x */
     int32_t prof_order;
     double prof_x0, prof_fwhm, prof_cut;
+    int32_t tf_mode;         /* 1: total-field run (Sec. 3.1 case (i), 1D plane wave only): the
+                                incident wave enters through the x = 0 face (its first-order
+                                absorbing condition acts on E - E_inc) and is not added at the
+                                particles; 0: scattered-field run */
     int32_t autotune_steps;  /* > 0: pic_init first runs pic_autotune with this many trial steps
                                 for a tile or chunk left at 0 (cached per shape) */
 } pic_config;

@@ -261,9 +261,11 @@ def derive_pulse(beam: int, w0: float, duration: float, a0: float):
     return a, s, psi0_from_a0(beam, a, s, a0)
 
 
-def config_from(w, field_bc: int = BC_MUR, tf_mode: int = 0) -> OrcConfig:
+def config_from(w, field_bc: int = BC_MUR, tf_mode: int = None) -> OrcConfig:
     """OrcConfig for a workload description (any object with the attributes of
     synth.Workload); LP/RP parameters not given explicitly are derived here."""
+    if tf_mode is None:
+        tf_mode = getattr(w, "tf_mode", 0)
     a, s, psi0 = w.a_param, w.s_param, w.psi0
     if w.beam in (BEAM_LP, BEAM_RP) and (a <= 0 or s <= 0 or psi0 <= 0):
         da, ds, dp = derive_pulse(w.beam, w.w0, w.duration, w.a0)

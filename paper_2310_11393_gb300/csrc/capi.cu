@@ -174,6 +174,8 @@ pic_status validate(const pic_config* c, pic_sim* s)
         if (!(c->w0 > 0) || !(c->duration > 0))
             return fail(s, PIC_EINVAL, "the 2D Gaussian beam needs w0 > 0 and duration > 0");
     }
+    if (c->tf_mode != 0 && (c->tf_mode != 1 || c->dim != 1 || c->beam != PIC_BEAM_PLANE))
+        return fail(s, PIC_EINVAL, "tf_mode = 1 needs dim == 1 and the plane wave");
     if (c->profile < PIC_PROFILE_UNIFORM || c->profile > PIC_PROFILE_SUPERGAUSS)
         return fail(s, PIC_EINVAL, "unknown profile %d", c->profile);
     if (c->profile == PIC_PROFILE_SUPERGAUSS && (!(c->prof_fwhm > 0) || c->prof_order < 1 || c->prof_order > 64))
@@ -595,6 +597,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.nytiles = L.nytiles;
     h.margin = cfg->remove_margin > 0 ? cfg->remove_margin : 3;
     h.pusher = cfg->pusher;
+    h.tf = cfg->tf_mode;
     h.dx = cfg->dx;
     h.dt = prm.dt;
     h.inv_dx = 1.0 / cfg->dx;

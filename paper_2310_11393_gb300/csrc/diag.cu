@@ -127,7 +127,7 @@ __global__ void k_energy_fields(const SimDev* __restrict__ sim, int m0, int m1, 
             const double f = (double)F[eb + comp * S.sc + o];
             es += 0.5 * f * f;
             double inc = 0.0;
-            if (S.beam != BEAM_NONE) {
+            if (S.beam != BEAM_NONE && !S.tf) {
                 R Ei[3], Bi[3];
                 const PhaseRef<R> pr = phase_ref<R>(S, t, cc[0]);
                 incident_at<D, R>(S, bc, pr, cc, oo, Ei, Bi);

@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
             B[1] = interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
             B[2] = interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
 
-            // ---- incident field at (x^n, t^n) ----
-            {
+            // ---- incident field at (x^n, t^n) (in a total-field run it is on the grid) ----
+            if (!S.tf) {
                 R Ei[3], Bi[3];
                 incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
 #pragma unroll

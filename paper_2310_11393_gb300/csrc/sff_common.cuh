@@ -75,6 +75,7 @@ struct alignas(128) SimDev {
     int cb[3];                // bits of each cell coordinate in the packed cell index
     int margin;
     int pusher;               // 0 Boris, 1 Vay, 2 Higuera-Cary
+    int tf;                   // total-field run: incident wave injected at x = 0, not at particles
     double dx, dt, inv_dx;
     // incident field
     double a0, duration, phi0, t_focus, a, s, psi0, w0;

@@ -16,6 +16,7 @@
 // reads in the same launch.
 #include <cuda_runtime.h>
 
+#include "beam.cuh"
 #include "sff_common.cuh"
 #include "sff_kernels.h"
 
@@ -200,6 +201,29 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
                         const int nb = i + dir * es[a];
                         const R* Eo = In + c * BV;
                         R* En = Jn + c * BV;
+                        if constexpr (D == 1) {
+                            if (S.tf && g[0] == 0) {
+                                // total-field run: the condition acts on E - E_inc, so the
+                                // plane wave (nodes x = 0 and dx, times t^n and t^{n+1}) enters
+                                R inc[2][2];
+                                const BeamC<R>& bcs = beam_of<R>(S);
+#pragma unroll
+                                for (int k = 0; k < 2; ++k) {
+                                    const PhaseRef<R> pr = phase_ref<R>(S, (double)(st->step + k) * S.dt, 0);
+#pragma unroll
+                                    for (int node = 0; node < 2; ++node) {
+                                        const int cc[3] = {node, 0, 0};
+                                        const R oo[3] = {R(0), R(0), R(0)};
+                                        R Ei[3], Bi[3];
+                                        incident_at<1, R>(S, bcs, pr, cc, oo, Ei, Bi);
+                                        inc[k][node] = Ei[c];
+                                    }
+                                }
+                                En[i] = inc[1][0] + (Eo[nb] - inc[0][1]) +
+                                        km * ((En[nb] - inc[1][1]) - (Eo[i] - inc[0][0]));
+                                continue;
+                            }
+                        }
                         En[i] = Eo[nb] + km * (En[nb] - Eo[i]);
                     }
                 }

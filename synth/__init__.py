@@ -64,6 +64,7 @@ class Workload:
     prof_x0: float = 0.0
     prof_fwhm: float = 1.0
     prof_cut: float = 0.0
+    tf_mode: int = 0                     # 1: total-field run, plane wave through x = 0 (1D)
 
     @property
     def dt(self) -> float:

@@ -78,6 +78,10 @@ def test_counts_and_footprint(P):
     (dict(tile=(6, 16, 1)), "tile"),
     (dict(n=(8, 1024, 1)), "n[0]"),
     (dict(chunk=1000), "chunk"),
+    (dict(tf_mode=1), "tf_mode"),
+    (dict(beam=5, w0=0.0), "Gaussian"),
+    (dict(profile=1, prof_fwhm=0.0), "super-Gaussian"),
+    (dict(pusher=3), "pusher"),
     (dict(chunk=32768), "chunk"),
 ])
 def test_invalid_configs_are_rejected(P, bad, frag):
