@@ -76,6 +76,7 @@ class OrcConfig(ctypes.Structure):
         ("prof_x0", ctypes.c_double),
         ("prof_fwhm", ctypes.c_double),
         ("prof_cut", ctypes.c_double),
+        ("incident_grid", ctypes.c_int),
     ]
 
 
@@ -277,4 +278,5 @@ def config_from(w, field_bc: int = BC_MUR, tf_mode: int = None) -> OrcConfig:
                        focus=w.focus, a=a, s=s, psi0=psi0, e_unif=w.e_unif, b_unif=w.b_unif,
                        slab_lo=w.slab_lo, slab_hi=w.slab_hi, n_e=w.n_e, ppc=w.ppc, seed=w.seed,
                        remove_margin=w.remove_margin, pusher=w.pusher, w0=w.w0, profile=w.profile,
-                       prof_order=w.prof_order, prof_x0=w.prof_x0, prof_fwhm=w.prof_fwhm, prof_cut=w.prof_cut)
+                       prof_order=w.prof_order, prof_x0=w.prof_x0, prof_fwhm=w.prof_fwhm, prof_cut=w.prof_cut,
+                       incident_grid=w.incident_grid)

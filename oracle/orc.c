@@ -385,6 +385,7 @@ struct orc_sim {
     int ext[3];        /* array extent per axis */
     int64_t nnode;
     double* F[9];      /* Ex Ey Ez Bx By Bz Jx Jy Jz */
+    double* Finc[6];   /* incident E, B on the Yee nodes at t^n (incident_grid runs only) */
     double* rho_ion;
     int64_t np, cap;
     double *px, *pu, *pw;
@@ -504,6 +505,7 @@ orc_sim* orc_create(const orc_config* cfg)
         s->nnode *= s->ext[d];
     }
     for (int c = 0; c < 9; c++) s->F[c] = calloc(s->nnode, sizeof(double));
+    for (int c = 0; c < 6; c++) s->Finc[c] = cfg->incident_grid ? calloc(s->nnode, sizeof(double)) : NULL;
     s->rho_ion = calloc(s->nnode, sizeof(double));
 
     /* seeded slab: slab cells in x-fastest order, ppc particles per cell; particle p
@@ -547,6 +549,7 @@ void orc_destroy(orc_sim* s)
 {
     if (!s) return;
     for (int c = 0; c < 9; c++) free(s->F[c]);
+    for (int c = 0; c < 6; c++) free(s->Finc[c]);
     free(s->rho_ion);
     free(s->px); free(s->pu); free(s->pw); free(s->pid);
     free(s->eu); free(s->ew); free(s->eid); free(s->estep);
@@ -599,7 +602,11 @@ void orc_set_fields(orc_sim* s, const double* in)
 }
 
 /* ---- gather -------------------------------------------------------------------- */
-static double gather(const orc_sim* s, int comp, const double X[3])
+static double gather_from(const orc_sim* s, const double* arr, int comp, const double X[3]);
+
+static double gather(const orc_sim* s, int comp, const double X[3]) { return gather_from(s, s->F[comp], comp, X); }
+
+static double gather_from(const orc_sim* s, const double* arr, int comp, const double X[3])
 {
     int lo[3], na[3];
     double w[3][3];
@@ -618,7 +625,8 @@ static double gather(const orc_sim* s, int comp, const double X[3])
         for (int b = 0; b < na[1]; b++)
             for (int a = 0; a < na[0]; a++) {
                 int idx[3] = {lo[0] + a, lo[1] + b, lo[2] + c};
-                v += w[0][a] * w[1][b] * w[2][c] * val(s, comp, idx);
+                v += w[0][a] * w[1][b] * w[2][c] *
+                     arr[IX(s, wrapi(s, 0, idx[0]), wrapi(s, 1, idx[1]), wrapi(s, 2, idx[2]))];
             }
     return v;
 }
@@ -910,6 +918,22 @@ static void push_higuera_cary(double u[3], const double E[3], const double B[3],
     for (int c = 0; c < 3; c++) u[c] = 2.0 * ub[c] - um[c] + h * E[c];
 }
 
+/* incident E, B of every component on its own Yee nodes at time t */
+static void incident_on_nodes(orc_sim* s, double t)
+{
+    for (int comp = 0; comp < 6; comp++)
+        for (int k = 0; k < s->ext[2]; k++)
+            for (int j = 0; j < s->ext[1]; j++)
+                for (int i = 0; i < s->ext[0]; i++) {
+                    int idx[3] = {i, j, k};
+                    double xp[3], Ei[3], Bi[3];
+                    for (int d = 0; d < 3; d++)
+                        xp[d] = s->res[d] ? (idx[d] + (staggered(comp, d) ? 0.5 : 0.0)) * s->c.dx : 0.0;
+                    orc_incident(&s->c, xp, t, Ei, Bi);
+                    s->Finc[comp][IX(s, i, j, k)] = comp < 3 ? Ei[comp] : Bi[comp - 3];
+                }
+}
+
 void orc_step(orc_sim* s, int nsteps)
 {
     const double dt = s->c.dt, dx = s->c.dx;
@@ -919,13 +943,20 @@ void orc_step(orc_sim* s, int nsteps)
         int64_t keep = 0;
         /* J of this step; it stays readable after the step as J^{n+1/2} */
         for (int c = 6; c < 9; c++) memset(s->F[c], 0, sizeof(double) * s->nnode);
+        const int inc_grid = s->c.incident_grid && s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode;
+        if (inc_grid) incident_on_nodes(s, t);
         for (int64_t p = 0; p < s->np; p++) {
             double* x = &s->px[3 * p];
             double* u = &s->pu[3 * p];
             double X[3] = {x[0] / dx, x[1] / dx, x[2] / dx};
             double E[3], B[3];
             for (int c = 0; c < 3; c++) { E[c] = gather(s, c, X); B[c] = gather(s, 3 + c, X); }
-            if (s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode) {
+            if (inc_grid) {
+                for (int c = 0; c < 3; c++) {
+                    E[c] += gather_from(s, s->Finc[c], c, X);
+                    B[c] += gather_from(s, s->Finc[3 + c], 3 + c, X);
+                }
+            } else if (s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode) {
                 double Ei[3], Bi[3];
                 orc_incident(&s->c, x, t, Ei, Bi);
                 for (int c = 0; c < 3; c++) { E[c] += Ei[c]; B[c] += Bi[c]; }

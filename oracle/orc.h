@@ -62,6 +62,9 @@ typedef struct {
     double prof_x0;       /* f(x) = 0 for x <= prof_cut, else 2^-[2 (x - prof_x0)/prof_fwhm]^p */
     double prof_fwhm;
     double prof_cut;
+    int incident_grid;    /* 1: the incident field is evaluated on the Yee nodes of each component at
+                             t^n and gathered with the scattered field (Smilei's prescribed-field
+                             route, Sec. 2 last paragraph); 0: at the particle (Sec. 2) */
 } orc_config;
 
 typedef struct orc_sim orc_sim;

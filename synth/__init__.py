@@ -65,6 +65,7 @@ class Workload:
     prof_fwhm: float = 1.0
     prof_cut: float = 0.0
     tf_mode: int = 0                     # 1: total-field run, plane wave through x = 0 (1D)
+    incident_grid: int = 0               # 1: incident field on the Yee nodes, gathered (prescribed-field route)
 
     @property
     def dt(self) -> float:

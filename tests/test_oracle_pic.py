@@ -9,6 +9,9 @@
   field, |u| kept in a pure B field, the force-free E x B drift of a relativistic
   electron kept to round-off (where Boris is off at O(dt^2) -- the property both were
   built for), gyration phase and plane-wave trajectory converging at second order;
+* the incident field evaluated on the Yee nodes and gathered (the prescribed-field route):
+  exact for a uniform field (the shapes sum to one), and the single-electron plane-wave
+  trajectory converging at second order as the cell and the step shrink together;
 * Gauss law div E - rho = 0 to round-off under Esirkepov deposition (2D and 3D, open
   and periodic);
 * the Yee vacuum dispersion relation sin^2(w dt/2)/dt^2 = sum_d sin^2(k_d dx/2)/dx^2
@@ -127,6 +130,44 @@ def _one_electron(orc, pusher, u0, steps, dt=0.1, E=(0.0, 0.0, 0.0), B=(0.0, 0.0
     sim.set_particles([[6.0, 0, 0]], [list(u0)], [0.0], [0])
     sim.step(steps)
     return sim.particles()["u"][0]
+
+
+def test_incident_on_the_grid_is_exact_for_a_uniform_field(orc):
+    E, B = (0.3, -0.2, 0.5), (0.1, 0.4, -0.7)
+    u0 = [0.5, 0.2, 0.1]
+    out = []
+    for grid in (0, 1):
+        c = cfg(orc, n=(64, 1, 1), dx=0.2, dt=0.1, field_bc=orc.BC_PERIODIC, beam=orc.BEAM_UNIFORM,
+                e_unif=E, b_unif=B, incident_grid=grid)
+        sim = orc.Sim(c)
+        sim.set_particles([[6.3, 0, 0]], [u0], [0.0], [0])
+        sim.step(50)
+        out.append(sim.particles()["u"][0])
+    assert np.abs(out[0] - out[1]).max() < 1e-13
+
+
+def test_incident_on_the_grid_converges_at_second_order(orc):
+    """Single electron in the sin^2 plane wave with the incident field on the nodes: the
+    closed-form trajectory error falls 4-fold when dx and dt halve together."""
+    a0, T = 1.5, 4 * math.pi
+    errs = []
+    for dx in (0.2, 0.1, 0.05):
+        dt = 0.95 * dx
+        n = int(round(600 / dx))
+        c = cfg(orc, n=(n, 1, 1), dx=dx, dt=dt, beam=orc.BEAM_PLANE, envelope=orc.ENV_SIN2, a0=a0, duration=T,
+                focus=(0.0, 0.0, 0.0), incident_grid=1)
+        sim = orc.Sim(c)
+        sim.set_particles([[40.0, 0, 0]], [[0, 0, 0]], [0.0], [0])
+        err = 0.0
+        for it in range(int((2 * T + 60.0) / dt)):
+            x_old = sim.particles()["x"][0, 0]
+            sim.step(1)
+            p = sim.particles()
+            xi = (it + 0.5) * dt - 0.5 * (x_old + p["x"][0, 0])
+            err = max(err, abs(p["u"][0][1] - _A_plane(xi, a0, T)))
+        errs.append(err)
+    assert errs[2] < 5e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
 
 
 @pytest.mark.parametrize("pusher", [0, 1, 2])
