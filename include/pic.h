@@ -123,6 +123,11 @@ typedef struct {
                                 incident wave enters through the x = 0 face (its first-order
                                 absorbing condition acts on E - E_inc) and is not added at the
                                 particles; 0: scattered-field run */
+    int32_t incident_grid;   /* 1: the incident field is evaluated once per step on the Yee nodes of
+                                each component (the prescribed-field route of Smilei, Sec. 2 last
+                                paragraph) and gathered with the scattered field, instead of at
+                                every particle: 2^dim closed-form evaluations per cell instead of
+                                ppc; interpolation error O((k dx)^2); 0: at the particle (Sec. 2) */
     int32_t autotune_steps;  /* > 0: pic_init first runs pic_autotune with this many trial steps
                                 for a tile or chunk left at 0 (cached per shape) */
 } pic_config;

@@ -102,6 +102,14 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         g.prec = kv.first.second;
         g.push_smem = psm;
         g.yee_smem = ysm;
+        g.inc_any = 0;
+        g.inc_segs = g.inc_rows = 1;
+        for (int i : mem) {
+            const pic_config& c = sims[i]->cfg;
+            g.inc_any |= sims[i]->h.incgrid;
+            g.inc_segs = std::max(g.inc_segs, (c.n[0] + 1 + 255) / 256);
+            g.inc_rows = std::max(g.inc_rows, (c.dim > 1 ? c.n[1] + 1 : 1) * (c.dim > 2 ? c.n[2] + 1 : 1));
+        }
         const int nsm = prop.multiProcessorCount;
         const int bp = std::max(1, sff::prepare_push(g.dim, g.prec, psm));
         const int byy = std::max(1, sff::prepare_yee(g.dim, g.prec, ysm));
@@ -119,6 +127,7 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
     }
     for (auto& gr : e->groups) {
         sff::launch_prefix(gr.g, e->cs);
+        sff::launch_incident_grid(gr.g, e->cs);
         sff::launch_push(gr.g, e->cs);
         sff::launch_scan(gr.g, e->cs);
         sff::launch_scatter(gr.g, e->cs);

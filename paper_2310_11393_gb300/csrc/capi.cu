@@ -149,7 +149,7 @@ pic_status fail(pic_sim* s, pic_status st, const char* fmt, ...)
     } while (0)
 
 struct Layout {
-    int dim, es;
+    int dim, es, ncomp;
     int n[3], na[3], pt[3], npt[3], pb[3], yt[3], nyt[3], yb[3], yo[3];
     long long sy, sz, sc, natot;
     int nptiles, nytiles;
@@ -174,6 +174,7 @@ pic_status validate(const pic_config* c, pic_sim* s)
         if (!(c->w0 > 0) || !(c->duration > 0))
             return fail(s, PIC_EINVAL, "the 2D Gaussian beam needs w0 > 0 and duration > 0");
     }
+    if (c->incident_grid != 0 && c->incident_grid != 1) return fail(s, PIC_EINVAL, "incident_grid must be 0 or 1");
     if (c->tf_mode != 0 && (c->tf_mode != 1 || c->dim != 1 || c->beam != PIC_BEAM_PLANE))
         return fail(s, PIC_EINVAL, "tf_mode = 1 needs dim == 1 and the plane wave");
     if (c->profile < PIC_PROFILE_UNIFORM || c->profile > PIC_PROFILE_SUPERGAUSS)
@@ -245,6 +246,7 @@ Layout make_layout(const pic_config* c)
     Layout L{};
     L.dim = c->dim;
     L.es = c->precision == PIC_FP64 ? 8 : 4;
+    L.ncomp = c->incident_grid ? NFCOMP_INC : NFCOMP;
     choose_tiles(c, L.pt, L.yt);
     for (int d = 0; d < 3; ++d) {
         if (d < c->dim) {
@@ -295,7 +297,7 @@ Layout make_layout(const pic_config* c)
                                    (size_t)(6 * ytv * L.es);
     size_t b = 0;
     b += align256(sizeof(SimDev)) + align256(sizeof(DevState));
-    b += align256((size_t)NFCOMP * L.natot * L.es);
+    b += align256((size_t)L.ncomp * L.natot * L.es);
     const size_t per = 4 + (size_t)(c->dim + 4) * L.es + 4;
     for (int q = 0; q < 2; ++q) {
         b += align256(L.cap * 4) * 2;                                  // cell, id
@@ -372,7 +374,7 @@ pic_status make_map(pic_sim* s, CUtensorMap* m, const Layout& L, const int box[3
         gdim[d] = (cuuint64_t)L.na[d];
         bdim[d] = (cuuint32_t)box[d];
     }
-    gdim[L.dim] = NFCOMP;
+    gdim[L.dim] = L.ncomp;
     bdim[L.dim] = (cuuint32_t)ncomp;
     const long long strides[3] = {L.sy, L.sz, L.sc};
     int k = 0;
@@ -408,6 +410,7 @@ pic_status capture_step(pic_sim* s)
     cudaStream_t cs = s->cap_stream;
     CU_CHECK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     launch_prefix(s->grp, cs);
+    launch_incident_grid(s->grp, cs);
     launch_push(s->grp, cs);
     launch_scan(s->grp, cs);
     launch_scatter(s->grp, cs);
@@ -543,7 +546,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     memset(&h, 0, sizeof h);
     s->d = (SimDev*)A.take(sizeof(SimDev));
     h.st = (DevState*)A.take(sizeof(DevState));
-    h.F = A.take((size_t)NFCOMP * L.natot * L.es);
+    h.F = A.take((size_t)L.ncomp * L.natot * L.es);
     for (int q = 0; q < 2; ++q) {
         h.cell[q] = (unsigned*)A.take(L.cap * 4);
         h.pid[q] = (unsigned*)A.take(L.cap * 4);
@@ -598,6 +601,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.margin = cfg->remove_margin > 0 ? cfg->remove_margin : 3;
     h.pusher = cfg->pusher;
     h.tf = cfg->tf_mode;
+    h.incgrid = cfg->incident_grid && cfg->beam != PIC_BEAM_NONE && !cfg->tf_mode;
     h.dx = cfg->dx;
     h.dt = prm.dt;
     h.inv_dx = 1.0 / cfg->dx;
@@ -651,7 +655,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
             return cleanup(PIC_ECUDA);                                                                \
         }                                                                                             \
     } while (0)
-    INIT_CHECK(cudaMemsetAsync(h.F, 0, (size_t)NFCOMP * L.natot * L.es, st));
+    INIT_CHECK(cudaMemsetAsync(h.F, 0, (size_t)L.ncomp * L.natot * L.es, st));
     INIT_CHECK(cudaMemsetAsync(h.toff[0], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.toff[1], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.coff[0], 0, (size_t)(L.nptiles + 1) * 4, st));
@@ -713,6 +717,9 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     const int bp = std::max(1, prepare_push(cfg->dim, cfg->precision, L.push_smem));
     const int by = std::max(1, prepare_yee(cfg->dim, cfg->precision, L.yee_smem));
     const int bs = std::max(1, scatter_blocks_per_sm(cfg->dim, cfg->precision));
+    g.inc_any = h.incgrid;
+    g.inc_segs = (cfg->n[0] + 1 + 255) / 256;
+    g.inc_rows = (cfg->dim > 1 ? cfg->n[1] + 1 : 1) * (cfg->dim > 2 ? cfg->n[2] + 1 : 1);
     g.push_grid = std::max(1, std::min(L.max_chunks, bp * nsm));
     g.yee_grid = std::max(1, std::min(L.nytiles, by * nsm));
     g.scatter_grid = std::max(1, std::min(L.max_chunks, bs * nsm));

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
             tensormap_acquire(&S.tm_pf);
             tensormap_acquire(&S.tm_pj);
             mbar_arrive_expect_tx(&bar, (unsigned)(6 * bvol * sizeof(R)));
-            tma_load_box<D>(Fs, &S.tm_pf, org, comp_eb(par), &bar);
+            tma_load_box<D>(Fs, &S.tm_pf, org, S.incgrid ? COMP_TOTAL : comp_eb(par), &bar);
             // double-precision phase reference of this tile, once per tile
             s_pref = phase_ref<R>(S, (double)st->step * S.dt, T0[0]);
         }
@@ -313,8 +313,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_
             B[1] = interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
             B[2] = interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
 
-            // ---- incident field at (x^n, t^n) (in a total-field run it is on the grid) ----
-            if (!S.tf) {
+            // ---- incident field at (x^n, t^n) (in a total-field run, or when it was
+            // evaluated on the grid, it is in the gathered field already) ----
+            if (!S.tf && !S.incgrid) {
                 R Ei[3], Bi[3];
                 incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
 #pragma unroll
@@ -714,6 +715,54 @@ __global__ void k_step_end(const SimDev* __restrict__ sims, int nsims)
     }
 }
 
+// Incident field on the Yee nodes (the prescribed-field route): one block per row segment of
+// 256 x-nodes (blockIdx.x = row * segs + segment) of one simulation (blockIdx.y); each node evaluates the closed form once per distinct
+// half-cell offset pattern of the staggered components (2^dim patterns, 2 in 1D, 4 in 2D,
+// 6 used in 3D) and writes total = scattered + incident into components COMP_TOTAL..+5.
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_incident_grid(const SimDev* __restrict__ sims, int segs)
+{
+    const SimDev& S = sims[blockIdx.y];
+    if (!S.incgrid) return;
+    const int ext0 = S.n[0] + 1, ext1 = D > 1 ? S.n[1] + 1 : 1, ext2 = D > 2 ? S.n[2] + 1 : 1;
+    const int row = blockIdx.x / segs, x0 = (blockIdx.x % segs) * 256;
+    if (row >= ext1 * ext2 || x0 >= ext0) return;
+    __shared__ PhaseRef<R> s_pr;
+    const DevState* st = S.st;
+    if (threadIdx.x == 0) s_pr = phase_ref<R>(S, (double)st->step * S.dt, x0);
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= ext0) return;
+    const int y = row % ext1, z = row / ext1;
+    const PhaseRef<R> pr = s_pr;
+    const BeamC<R>& bc = beam_of<R>(S);
+    R* F = reinterpret_cast<R*>(S.F);
+    const long long base = (long long)(D > 2 ? z + G : 0) * S.sz + (long long)(D > 1 ? y + G : 0) * S.sy + (x + G);
+    const long long eb = (long long)comp_eb(st->parity) * S.sc;
+    const long long tb = (long long)COMP_TOTAL * S.sc;
+    const int c[3] = {x, y, z};
+#pragma unroll
+    for (int m = 0; m < (1 << D); ++m) {
+        // components whose stagger pattern is m: E_q half a cell along axis q, B_q along the others
+        int mask = 0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            int pat = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                if (q < 3 ? d == q : d != q - 3) pat |= 1 << d;
+            if (pat == m) mask |= 1 << q;
+        }
+        if (!mask) continue;
+        const R o[3] = {(m & 1) ? R(0.5) : R(0), (m & 2) ? R(0.5) : R(0), (m & 4) ? R(0.5) : R(0)};
+        R Ei[3], Bi[3];
+        incident_at<D, R>(S, bc, pr, c, o, Ei, Bi);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (mask & (1 << q)) F[tb + q * S.sc + base] = F[eb + q * S.sc + base] + (q < 3 ? Ei[q] : Bi[q - 3]);
+    }
+}
+
 // ---- set-up ----------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long k)
 {
@@ -819,6 +868,27 @@ void launch_scatter(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec
 void launch_scan(const Group& g, cudaStream_t s) { k_scan<<<g.nsims, 1024, 0, s>>>(g.sims); }
 void launch_prefix(const Group& g, cudaStream_t s) { k_prefix<<<1, 1024, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters); }
 void launch_step_end(const Group& g, cudaStream_t s) { k_step_end<<<1, 256, 0, s>>>(g.sims, g.nsims); }
+
+template <int D, typename R>
+static void incgrid_t(const Group& g, cudaStream_t s)
+{
+    const dim3 grid((unsigned)g.inc_segs * (unsigned)g.inc_rows, g.nsims);
+    k_incident_grid<D, R><<<grid, 256, 0, s>>>(g.sims, g.inc_segs);
+}
+
+void launch_incident_grid(const Group& g, cudaStream_t s)
+{
+    if (!g.inc_any) return;
+    if (g.prec == 0) {
+        if (g.dim == 1) incgrid_t<1, double>(g, s);
+        else if (g.dim == 2) incgrid_t<2, double>(g, s);
+        else incgrid_t<3, double>(g, s);
+    } else {
+        if (g.dim == 1) incgrid_t<1, float>(g, s);
+        else if (g.dim == 2) incgrid_t<2, float>(g, s);
+        else incgrid_t<3, float>(g, s);
+    }
+}
 void launch_scan_one(const SimDev* sim, int, int, cudaStream_t s) { k_scan_one<<<1, 1024, 0, s>>>(sim); }
 
 template <int D, typename R>

@@ -76,6 +76,7 @@ struct alignas(128) SimDev {
     int margin;
     int pusher;               // 0 Boris, 1 Vay, 2 Higuera-Cary
     int tf;                   // total-field run: incident wave injected at x = 0, not at particles
+    int incgrid;              // incident field on the grid (components COMP_TOTAL..+5 hold the total)
     double dx, dt, inv_dx;
     // incident field
     double a0, duration, phi0, t_focus, a, s, psi0, w0;

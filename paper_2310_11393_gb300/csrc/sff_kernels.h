@@ -13,6 +13,9 @@ namespace sff {
 // The push reads set p and deposits J_p; the field solver reads set p and J_p, writes
 // set 1-p and clears J_{1-p}.  p = DevState::parity flips at the end of each step.
 constexpr int NFCOMP = 18;
+// With the incident field on the grid, components 18..23 hold E, B of the total field at t^n
+// (scattered + incident), which the push gathers.
+constexpr int COMP_TOTAL = 18, NFCOMP_INC = 24;
 __host__ __device__ constexpr int comp_eb(int parity) { return 6 * parity; }
 __host__ __device__ constexpr int comp_j(int parity) { return 12 + 3 * parity; }
 
@@ -29,6 +32,7 @@ struct Group {
     int dim, prec;
     size_t push_smem, yee_smem;
     int push_grid, yee_grid, scatter_grid;
+    int inc_any, inc_segs, inc_rows;   // incident field on the grid: any member, x segments, rows
 };
 
 // 3D field solver: columns of Y3_PX x Y3_PY points (x, y) marching along z through a
@@ -49,6 +53,7 @@ void launch_scan(const Group& g, cudaStream_t s);
 void launch_scatter(const Group& g, cudaStream_t s);
 void launch_yee(const Group& g, cudaStream_t s);
 void launch_step_end(const Group& g, cudaStream_t s);
+void launch_incident_grid(const Group& g, cudaStream_t s);
 
 // set-up: particles written linearly into buffer set 1, then sorted into set 0
 void launch_gen_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int slab_lo[3],

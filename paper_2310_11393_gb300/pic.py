@@ -35,7 +35,7 @@ class pic_config(Structure):
         ("n_e", c_double), ("ppc", c_int32), ("tile", c_int32 * 3), ("seed", c_uint64),
         ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("pusher", c_int32), ("profile", c_int32), ("prof_order", c_int32),
         ("prof_x0", c_double), ("prof_fwhm", c_double), ("prof_cut", c_double), ("tf_mode", c_int32),
-        ("autotune_steps", c_int32),
+        ("incident_grid", c_int32), ("autotune_steps", c_int32),
     ]
 
 
@@ -343,6 +343,7 @@ def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chun
     c.prof_fwhm = getattr(w, "prof_fwhm", 1.0)
     c.prof_cut = getattr(w, "prof_cut", 0.0)
     c.tf_mode = getattr(w, "tf_mode", 0)
+    c.incident_grid = getattr(w, "incident_grid", 0)
     return c
 
 
