@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
     ap.add_argument("--autotune", type=int, default=10,
                     help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
+    ap.add_argument("--incident", default="particle", choices=["particle", "grid"],
+                    help="incident field at every particle (Sec. 2) or on the Yee nodes, gathered")
     ap.add_argument("--sims", type=int, default=256, help="batch: number of simulations")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (1/s)")
@@ -54,6 +56,7 @@ def parse():
 
 
 SCALE = 1
+INCIDENT_GRID = 0
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from the
 # ncu capture summarised in profiles/ (kept in step with the kernel: set to None when the
@@ -63,7 +66,8 @@ PROFILED_TRAFFIC = {("2d_lp_1024sq", "k_push<2,float>"): (75.3e6, "profiles/k_pu
 
 def workload(name):
     w = {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp, "2d_gauss": synth.c6_2d_gauss}[name]()
-    return w if SCALE == 1 else synth.scaled(w, SCALE)
+    w = w if SCALE == 1 else synth.scaled(w, SCALE)
+    return w.with_(incident_grid=INCIDENT_GRID, name=w.name + ("_incgrid" if INCIDENT_GRID else ""))
 
 
 def peaks():
@@ -142,6 +146,8 @@ def flops_per_push(w):
     # three partial sums per transverse node, 2D Jz / 3D every component over 4^(D-1) nodes
     deposit = {1: 40, 2: 300, 3: 970}[D]
     incident = {synth.BEAM_LP: 280, synth.BEAM_RP: 270, synth.BEAM_PLANE: 25, synth.BEAM_GAUSS2D: 45}.get(w.beam, 0)
+    if w.incident_grid:       # one evaluation per distinct stagger pattern per cell, shared by ppc
+        incident = incident * {1: 2, 2: 4, 3: 6}[D] / max(w.ppc, 1)
     move = 5 * D
     return gather + boris + deposit + incident + move
 
@@ -499,8 +505,9 @@ def run_serve(args):
 
 def main():
     args = parse()
-    global SCALE
+    global SCALE, INCIDENT_GRID
     SCALE = max(1, args.scale)
+    INCIDENT_GRID = 1 if args.incident == "grid" else 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
