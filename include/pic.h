@@ -198,8 +198,9 @@ pic_status pic_step(pic_sim* sim, int n_steps, void* stream);
 
 /* Advances n_steps steps like pic_step but launches the kernels one by one with CUDA
  * events recorded on `stream` between the phases, and returns in HOST seconds[5] the
- * summed device time of each phase: [0] push + deposit, [1] tile scan, [2] particle
- * scatter, [3] field solve, [4] step end.  Synchronous.  Used to time kernels live. */
+ * summed device time of each phase: [0] push + deposit (with incident_grid: also the
+ * evaluation of the incident field on the grid), [1] tile scan, [2] particle scatter,
+ * [3] field solve, [4] step end.  Synchronous.  Used to time kernels live. */
 pic_status pic_profile_step(pic_sim* sim, int n_steps, void* stream, double* seconds);
 
 /* Releases all device state; synchronises the simulation's work first.  NULL is a no-op. */

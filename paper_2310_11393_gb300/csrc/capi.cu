@@ -750,6 +750,7 @@ pic_status pic_profile_step(pic_sim* s, int n_steps, void* stream, double* secon
     for (int k = 0; k < n_steps && r == PIC_OK; ++k) {
         launch_prefix(s->grp, st);
         cudaEventRecord(ev[0], st);
+        launch_incident_grid(s->grp, st);
         launch_push(s->grp, st);
         cudaEventRecord(ev[1], st);
         launch_scan(s->grp, st);
