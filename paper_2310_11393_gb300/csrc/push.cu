@@ -195,7 +195,7 @@ __device__ __forceinline__ void higuera_cary_update(R u[3], const R E[3], const 
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 3 : 2)) k_push(const SimDev* __restrict__ sims, int nsims,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_push(const SimDev* __restrict__ sims, int nsims,
                                               const int* __restrict__ gprefix, int* __restrict__ counter)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
