@@ -103,6 +103,7 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         g.push_smem = psm;
         g.yee_smem = ysm;
         g.inc_any = 0;
+        g.scan_blocks = n == 1 ? sims[mem[0]]->h.nscanblk : 0;
         g.inc_segs = g.inc_rows = 1;
         for (int i : mem) {
             const pic_config& c = sims[i]->cfg;

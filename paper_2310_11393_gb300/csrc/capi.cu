@@ -305,6 +305,7 @@ Layout make_layout(const pic_config* c)
     }
     (void)per;
     b += 4 * align256((size_t)(L.nptiles + 1) * 4) + 2 * align256((size_t)L.nptiles * 4);
+    b += align256((size_t)((L.nptiles + 4095) / 4096) * 8) + align256(4);
     b += 2 * align256((size_t)L.max_chunks * 4);
     b += align256((size_t)L.max_exits * EXIT_DOUBLES * 8);
     b += 2 * align256((size_t)L.natot * 8);
@@ -567,6 +568,9 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.max_chunks = L.max_chunks;
     h.tcnt = (int*)A.take((size_t)L.nptiles * 4);
     h.tcur = (int*)A.take((size_t)L.nptiles * 4);
+    h.nscanblk = (L.nptiles + 4095) / 4096;
+    h.scanflags = (unsigned long long*)A.take((size_t)h.nscanblk * 8);
+    h.scanticket = (int*)A.take(4);
     h.exits = (double*)A.take((size_t)L.max_exits * EXIT_DOUBLES * 8);
     h.rho_ion = (double*)A.take((size_t)L.natot * 8);
     h.scratch = (double*)A.take((size_t)L.natot * 8);
@@ -662,6 +666,8 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     INIT_CHECK(cudaMemsetAsync(h.coff[1], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcnt, 0, (size_t)L.nptiles * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcur, 0, (size_t)L.nptiles * 4, st));
+    INIT_CHECK(cudaMemsetAsync(h.scanflags, 0, (size_t)h.nscanblk * 8, st));
+    INIT_CHECK(cudaMemsetAsync(h.scanticket, 0, 4, st));
     INIT_CHECK(cudaMemsetAsync(s->d_counters, 0, 64, st));
     INIT_CHECK(cudaMemsetAsync(h.rho_ion, 0, (size_t)L.natot * 8, st));
     DevState ds{};
@@ -718,6 +724,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     const int by = std::max(1, prepare_yee(cfg->dim, cfg->precision, L.yee_smem));
     const int bs = std::max(1, scatter_blocks_per_sm(cfg->dim, cfg->precision));
     g.inc_any = h.incgrid;
+    g.scan_blocks = h.nscanblk;
     g.inc_segs = (cfg->n[0] + 1 + 255) / 256;
     g.inc_rows = (cfg->dim > 1 ? cfg->n[1] + 1 : 1) * (cfg->dim > 2 ? cfg->n[2] + 1 : 1);
     g.push_grid = std::max(1, std::min(L.max_chunks, bp * nsm));

@@ -621,8 +621,104 @@ __global__ void __launch_bounds__(1024) k_scan_one(const SimDev* __restrict__ si
     scan_counts(*sim, 1 - sim->st->parity);
 }
 
+// Tile scan of one simulation over several blocks (decoupled look-back): block b (in the
+// order blocks start, from a ticket) scans tiles [4096 b, 4096 (b + 1)), publishes its
+// aggregate, then adds the totals of the blocks before it -- each published as
+// (status << 62) | (particles << 31) | chunks, status 1 aggregate, 2 inclusive prefix --
+// waiting (bounded) only on blocks that started earlier.  A wait that gives up flags a
+// timeout and takes prefix 0, which keeps every offset inside the particle arrays.
+__global__ void __launch_bounds__(1024) k_scan_lb(const SimDev* __restrict__ sims)
+{
+    const SimDev& S = sims[0];
+    __shared__ int s_warp[32];
+    __shared__ int s_cnt[4096];
+    __shared__ int s_b, s_tp, s_tc, s_pp, s_pc;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_b = atomicAdd(S.scanticket, 1);
+    __syncthreads();
+    const int b = s_b, n = S.nptiles, base = b * 4096;
+    const int outpar = 1 - S.st->parity;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + k * 1024 + tid;
+        s_cnt[k * 1024 + tid] = i < n ? S.tcnt[i] : 0;
+    }
+    __syncthreads();
+    int c4[4], lp = 0, lc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c4[k] = s_cnt[tid * 4 + k];
+        lp += c4[k];
+        lc += (c4[k] + S.chunk - 1) / S.chunk;
+    }
+    int rp = block_exclusive_scan(lp, s_warp);
+    int rc = block_exclusive_scan(lc, s_warp);
+    if (tid == 1023) {
+        s_tp = rp + lp;
+        s_tc = rc + lc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long* fl = S.scanflags;
+        const unsigned long long agg = ((unsigned long long)s_tp << 31) | (unsigned long long)s_tc;
+        long long pp = 0, pc = 0;
+        if (b == 0) {
+            atomicExch(&fl[0], (2ull << 62) | agg);
+        } else {
+            atomicExch(&fl[b], (1ull << 62) | agg);
+            bool ok = true;
+            for (int j = b - 1; j >= 0; --j) {
+                unsigned long long f = 0;
+                int spins = 0;
+                do {
+                    f = *reinterpret_cast<volatile unsigned long long*>(&fl[j]);
+                } while ((f >> 62) == 0 && ++spins < (1 << 22));
+                if ((f >> 62) == 0) {
+                    ok = false;
+                    break;
+                }
+                pp += (long long)((f >> 31) & 0x7FFFFFFFull);
+                pc += (long long)(f & 0x7FFFFFFFull);
+                if ((f >> 62) == 2) break;
+            }
+            if (!ok) {
+                atomicOr(&S.st->status, (unsigned)FLAG_TIMEOUT);
+                pp = pc = 0;
+            }
+            atomicExch(&fl[b], (2ull << 62) | ((unsigned long long)(pp + s_tp) << 31) |
+                                   (unsigned long long)(pc + s_tc));
+        }
+        s_pp = (int)pp;
+        s_pc = (int)pc;
+    }
+    __syncthreads();
+    rp += s_pp;
+    rc += s_pc;
+    int* to = S.toff[outpar];
+    int* co = S.coff[outpar];
+    int* ct = S.ctile[outpar];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = base + tid * 4 + k;
+        if (i >= n) break;
+        const int c = c4[k];
+        const int nc = (c + S.chunk - 1) / S.chunk;
+        to[i] = rp;
+        co[i] = rc;
+        for (int q = 0; q < nc; ++q) ct[rc + q] = i;
+        rp += c;
+        rc += nc;
+        S.tcnt[i] = 0;
+        S.tcur[i] = 0;
+        if (i == n - 1) {
+            to[n] = rp;
+            co[n] = rc;
+        }
+    }
+}
+
 // First node of every step: number the chunks of the group's simulations and reset the
-// work counters.
+// work counters (and the multi-block scan's flags of a single simulation).
 __global__ void __launch_bounds__(1024) k_prefix(const SimDev* __restrict__ sims, int nsims, int* __restrict__ gprefix,
                                                  int* __restrict__ counters)
 {
@@ -639,6 +735,11 @@ __global__ void __launch_bounds__(1024) k_prefix(const SimDev* __restrict__ sims
     }
     if (tid == nth - 1) gprefix[nsims] = r;
     if (tid < 4) counters[tid] = 0;
+    if (nsims == 1) {
+        const SimDev& S = sims[0];
+        for (int j = tid; j < S.nscanblk; j += nth) S.scanflags[j] = 0ull;
+        if (tid == 0) *S.scanticket = 0;
+    }
 }
 
 template <int D, typename R>
@@ -865,7 +966,12 @@ static void scatter_t(const Group& g, cudaStream_t s)
 
 void launch_push(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, push_t, g, s); }
 void launch_scatter(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, scatter_t, g, s); }
-void launch_scan(const Group& g, cudaStream_t s) { k_scan<<<g.nsims, 1024, 0, s>>>(g.sims); }
+void launch_scan(const Group& g, cudaStream_t s)
+{
+    // a single simulation scans its tiles over several blocks; a batch, one block per member
+    if (g.nsims == 1) k_scan_lb<<<g.scan_blocks, 1024, 0, s>>>(g.sims);
+    else k_scan<<<g.nsims, 1024, 0, s>>>(g.sims);
+}
 void launch_prefix(const Group& g, cudaStream_t s) { k_prefix<<<1, 1024, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters); }
 void launch_step_end(const Group& g, cudaStream_t s) { k_step_end<<<1, 256, 0, s>>>(g.sims, g.nsims); }
 

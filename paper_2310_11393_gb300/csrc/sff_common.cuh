@@ -102,6 +102,9 @@ struct alignas(128) SimDev {
     int max_chunks;
     int* tcnt;                // per-tile counts of the next step
     int* tcur;                // per-tile write cursors
+    unsigned long long* scanflags;   // multi-block tile scan: per block status | particles | chunks
+    int* scanticket;          // multi-block tile scan: block order ticket
+    int nscanblk;             // blocks of the multi-block tile scan (tiles / 4096, rounded up)
     double* exits;            // [max_exits][EXIT_DOUBLES]
     long long max_exits;
     long long cap;            // particle capacity per buffer set

@@ -33,6 +33,7 @@ struct Group {
     size_t push_smem, yee_smem;
     int push_grid, yee_grid, scatter_grid;
     int inc_any, inc_segs, inc_rows;   // incident field on the grid: any member, x segments, rows
+    int scan_blocks;                   // single simulation: blocks of the multi-block tile scan
 };
 
 // 3D field solver: columns of Y3_PX x Y3_PY points (x, y) marching along z through a
