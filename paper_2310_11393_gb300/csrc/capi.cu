@@ -293,8 +293,8 @@ Layout make_layout(const pic_config* c)
     const long long ytv = (long long)L.yt[0] * L.yt[1] * L.yt[2];
     L.push_smem = round128((size_t)(6 * pbv * L.es)) + (size_t)(3 * pbv * L.es);
     L.yee_smem = c->dim == 3 ? yee3_smem(L.es)
-                             : round128(round128((size_t)(6 * ybv * L.es)) + (size_t)(3 * ybv * L.es)) +
-                                   (size_t)(6 * ytv * L.es);
+                             : 2 * round128(round128((size_t)(6 * ybv * L.es)) + (size_t)(3 * ybv * L.es)) +
+                                   (size_t)(6 * ytv * L.es);      // two box buffers + the output tile
     size_t b = 0;
     b += align256(sizeof(SimDev)) + align256(sizeof(DevState));
     b += align256((size_t)L.ncomp * L.natot * L.es);

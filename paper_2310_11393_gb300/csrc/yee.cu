@@ -56,61 +56,80 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
     constexpr int EX = TX + 2 * HX, EY = TY + 2 * HY, EZ = TZ + 2 * HZ;
     constexpr int SY = EX, SZ = EX * EY, BV = EX * EY * EZ, TV = TX * TY * TZ;
     constexpr size_t JOFF = round128(6 * BV * sizeof(R));
-    constexpr size_t OOFF = round128(JOFF + 3 * BV * sizeof(R));
+    constexpr size_t BOXB = round128(JOFF + 3 * BV * sizeof(R));   // one box buffer
+    constexpr size_t OOFF = 2 * BOXB;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_item;
     const int tid = threadIdx.x;
     constexpr int NT = 256;
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    unsigned phase = 0;
-    R* In = reinterpret_cast<R*>(smem_raw);            // [6][EZ][EY][EX]: Ex Ey Ez Bx By Bz
-    R* Jn = reinterpret_cast<R*>(smem_raw + JOFF);     // [3][EZ][EY][EX]: J, then E^{n+1}
+    unsigned phases = 0;     // mbarrier phase per buffer
     R* Out = reinterpret_cast<R*>(smem_raw + OOFF);    // [6][TZ][TY][TX]
-    R* Ex = In;
-    R* Ey = In + BV;
-    R* Ez = In + 2 * BV;
-    R* Bx = In + 3 * BV;
-    R* By = In + 4 * BV;
-    R* Bz = In + 5 * BV;
-    R* Nx = Jn;
-    R* Ny = Jn + BV;
-    R* Nz = Jn + 2 * BV;
-    for (;;) {
+    // Two box buffers: while a block computes one tile, the TMA loads of its next tile (taken
+    // from the work counter one tile ahead) land in the other.
+    auto fetch = [&]() {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
-        const int item = s_item;
+        const int it = s_item;
         __syncthreads();
-        if (item >= nwork) break;
+        return it;
+    };
+    auto tile_lo = [&](const SimDev& S, int tile, int lo[3]) {
+        int t = tile;
+        lo[0] = (t % S.nyt[0]) * TX;
+        t /= S.nyt[0];
+        lo[1] = lo[2] = 0;
+        if constexpr (D > 1) {
+            lo[1] = (t % S.nyt[1]) * TY;
+            t /= S.nyt[1];
+        }
+        if constexpr (D > 2) lo[2] = t * TZ;
+    };
+    auto issue = [&](int it, int b) {
+        if (tid != 0) return;
+        const Work w = work[it];
+        const SimDev& S = sims[w.sim];
+        int l[3];
+        tile_lo(S, w.tile, l);
+        const int o[3] = {l[0] - HX + G, D > 1 ? l[1] - HY + G : 0, D > 2 ? l[2] - HZ + G : 0};
+        const int p = S.st->parity;
+        tensormap_acquire(&S.tm_yin);
+        tensormap_acquire(&S.tm_yj);
+        tensormap_acquire(&S.tm_yout);
+        unsigned char* box = smem_raw + b * BOXB;
+        mbar_arrive_expect_tx(&bars[b], (unsigned)(9 * BV * sizeof(R)));
+        tma_load_box<D>(box, &S.tm_yin, o, comp_eb(p), &bars[b]);
+        tma_load_box<D>(box + JOFF, &S.tm_yj, o, comp_j(p), &bars[b]);
+    };
+    int item = fetch();
+    if (item < nwork) issue(item, 0);
+    int buf = 0;
+    while (item < nwork) {
+        const int next = fetch();
+        if (next < nwork) issue(next, buf ^ 1);
+        R* In = reinterpret_cast<R*>(smem_raw + buf * BOXB);        // [6][EZ][EY][EX]: Ex Ey Ez Bx By Bz
+        R* Jn = reinterpret_cast<R*>(smem_raw + buf * BOXB + JOFF); // [3][EZ][EY][EX]: J, then E^{n+1}
+        R* Ex = In;
+        R* Ey = In + BV;
+        R* Ez = In + 2 * BV;
+        R* Bx = In + 3 * BV;
+        R* By = In + 4 * BV;
+        R* Bz = In + 5 * BV;
+        R* Nx = Jn;
+        R* Ny = Jn + BV;
+        R* Nz = Jn + 2 * BV;
         const Work wk = work[item];
         const SimDev& S = sims[wk.sim];
         DevState* st = S.st;
         const int par = st->parity;
-        int tc[3] = {0, 0, 0};
-        {
-            int t = wk.tile;
-            tc[0] = t % S.nyt[0];
-            t /= S.nyt[0];
-            if constexpr (D > 1) {
-                tc[1] = t % S.nyt[1];
-                t /= S.nyt[1];
-            }
-            if constexpr (D > 2) tc[2] = t;
-        }
-        const int lo[3] = {tc[0] * TX, tc[1] * TY, tc[2] * TZ};
-        const int org[3] = {lo[0] - HX + G, D > 1 ? lo[1] - HY + G : 0, D > 2 ? lo[2] - HZ + G : 0};
-        if (tid == 0) {
-            tensormap_acquire(&S.tm_yin);
-            tensormap_acquire(&S.tm_yj);
-            tensormap_acquire(&S.tm_yout);
-            mbar_arrive_expect_tx(&bar, (unsigned)(9 * BV * sizeof(R)));
-            tma_load_box<D>(In, &S.tm_yin, org, comp_eb(par), &bar);
-            tma_load_box<D>(Jn, &S.tm_yj, org, comp_j(par), &bar);
-        }
+        int lo[3];
+        tile_lo(S, wk.tile, lo);
         // the box reaches global points lo - h .. lo - h + E - 1; phases use 1 .. E - 2
         bool interior = true;
         {
@@ -122,12 +141,14 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
         }
         const YeeC<R>& yc = yee_of<R>(S);
         const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
-        const bool ok = mbar_wait_bounded(&bar, phase);
-        phase ^= 1u;
+        const bool ok = mbar_wait_bounded(&bars[buf], (phases >> buf) & 1u);
+        phases ^= 1u << buf;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(&st->status, (unsigned)FLAG_TIMEOUT);
-                mbar_wait_bounded(&bar, phase ^ 1u);
+                // let the loads still in flight (this tile's, and the next one's) land
+                if (!ok) mbar_wait_bounded(&bars[buf], ((phases >> buf) & 1u) ^ 1u);
+                if (next < nwork) mbar_wait_bounded(&bars[buf ^ 1], (phases >> (buf ^ 1)) & 1u);
                 bulk_wait0();
             }
             return;
@@ -271,7 +292,12 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
             }
         }
         if (tid == 0) bulk_wait_read0();
+        // this buffer was written by the phases above; the TMA load of the tile after next
+        // reuses it (generic-proxy writes before async-proxy writes to the same memory)
+        fence_proxy_async_smem();
         __syncthreads();
+        item = next;
+        buf ^= 1;
     }
     if (tid == 0) bulk_wait0();
 }
