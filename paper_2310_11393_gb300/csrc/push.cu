@@ -274,7 +274,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         // consecutive cells, so the same stencil node of the deposit and the gather is a
         // different shared-memory word (mostly a different bank) in every lane.
         const int P = S.lane_p, wq = tid >> 5;
-        const int q = (tid & 31) * P + (wq & (P - 1)) + 32 * P * (wq / P);
+        int q = (tid & 31) * P + (wq & (P - 1)) + 32 * P * (wq / P);
+        if (S.pt[0] == 16 && P <= 4) {
+            // 16-cell tile rows: a warp's 32 cells span two rows.  The box row pitch is 24
+            // words, so rows two apart start 16 banks apart: the warp's groups take rows
+            // (r, r + 2) of the round instead of (r, r + 1), and its two half-warps hit
+            // disjoint banks.
+            const int g = wq / P, l = tid & 31;
+            const int row = ((g >> 1) << 2) + (g & 1) + ((l >> 4) << 1);
+            q = (row * 16 + (l & 15)) * P + (wq & (P - 1));
+        }
         for (int rb = p0; rb < p1; rb += nth) {
             const int p = rb + q;
             if (p >= p1) continue;
