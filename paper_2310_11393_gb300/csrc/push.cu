@@ -495,10 +495,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                     atomicOr(&st->status, (unsigned)FLAG_EXIT_OVERFLOW);
                 }
             } else {
+                // destination tile relative to this one (a move is under one cell per axis)
                 int hidx = 0, mul = 1;
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    hidx += (cn[d] / S.pt[d] - tc[d] + 1) * mul;
+                    hidx += (cn[d] < T0[d] ? 0 : (cn[d] >= T0[d] + S.pt[d] ? 2 : 1)) * mul;
                     mul *= 3;
                 }
                 atomicAdd(&s_hist[hidx], 1);
