@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "2d_gauss", "batch", "serve"])
     ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
+    ap.add_argument("--tile", default="", help="particle tile, e.g. 16,8,4 (skips the autotuner's tile search)")
     ap.add_argument("--autotune", type=int, default=10,
                     help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
     ap.add_argument("--incident", default="particle", choices=["particle", "grid"],
@@ -190,7 +191,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = workload(args.workload)
-    cfg = pic.config_from(w)
+    tile = [int(v) for v in args.tile.split(",")] if args.tile else None
+    cfg = pic.config_from(w, tile=tile)
     stream = torch.cuda.current_stream(dev).cuda_stream
     alloc = pic.torch_allocator(local_rank)
     # tile and work-item size: measured by the autotuner (untimed set-up)
