@@ -693,7 +693,9 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
                         cfg->n_e / cfg->ppc, st);
         INIT_CHECK(cudaGetLastError());
         launch_scan_one(s->d, cfg->dim, cfg->precision, st);
-        launch_sort_linear(s->d, cfg->dim, cfg->precision, L.nslab, st);
+        int hi[3] = {1, 1, 1};
+        for (int d = 0; d < cfg->dim; ++d) hi[d] = cfg->slab_hi[d];
+        launch_place_slab(s->d, cfg->dim, cfg->precision, L.nslab, cfg->ppc, lo, hi, st);
         INIT_CHECK(cudaGetLastError());
     }
     ds.parity = 0;

@@ -949,6 +949,32 @@ __global__ void k_sort_linear(const SimDev* __restrict__ sim, long long n)
     }
 }
 
+// Seeded slab, set 1 (generation order: ppc particles per slab cell, x fastest) -> set 0,
+// placed directly in cell order within each tile: a particle of cell c goes to
+// toff[tile] + (rank of c among the tile's slab cells, x fastest) ppc + (its index in c).
+template <int D, typename R>
+__global__ void k_place_slab(const SimDev* __restrict__ sim, long long n, int ppc, int lo0, int lo1, int lo2,
+                             int hi0, int hi1, int hi2)
+{
+    const SimDev& S = *sim;
+    const int slo[3] = {lo0, lo1, lo2}, shi[3] = {hi0, hi1, hi2};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        decode_cell<D>(S, S.cell[1][p], c);
+        const int t = tile_of<D>(S, c);
+        long long rank = 0, width = 1;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int a = max(slo[d], (c[d] / S.pt[d]) * S.pt[d]);
+            const int b = min(shi[d], (c[d] / S.pt[d] + 1) * S.pt[d]);
+            rank += (c[d] - a) * width;
+            width *= (b - a);
+        }
+        copy_particle<D, R>(S, 1, p, 0, (long long)S.toff[0][t] + rank * ppc + (p % ppc));
+    }
+}
+
 // ---- host launch wrappers ------------------------------------------------------------
 template <int D, typename R>
 static void push_t(const Group& g, cudaStream_t s)
@@ -1037,6 +1063,18 @@ static void sortlin_t(const SimDev* sim, long long n, cudaStream_t s)
     const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
     if (n > 0) k_sort_linear<D, R><<<grid, 256, 0, s>>>(sim, n);
 }
+template <int D, typename R>
+static void place_t(const SimDev* sim, long long n, int ppc, const int lo[3], const int hi[3], cudaStream_t s)
+{
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (n > 0) k_place_slab<D, R><<<grid, 256, 0, s>>>(sim, n, ppc, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
+}
+void launch_place_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int lo[3], const int hi[3],
+                       cudaStream_t s)
+{
+    SFF_DISPATCH(dim, prec, place_t, sim, n, ppc, lo, hi, s);
+}
+
 void launch_sort_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s)
 {
     SFF_DISPATCH(dim, prec, sortlin_t, sim, n, s);

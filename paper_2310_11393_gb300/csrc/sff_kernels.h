@@ -61,6 +61,8 @@ void launch_gen_slab(const SimDev* sim, int dim, int prec, long long n, int ppc,
                      const int slab_n[3], unsigned long long seed, double weight, cudaStream_t s);
 void launch_count_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s);
 void launch_sort_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s);
+void launch_place_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int lo[3], const int hi[3],
+                       cudaStream_t s);
 void launch_scan_one(const SimDev* sim, int dim, int prec, cudaStream_t s);
 
 // diagnostics
