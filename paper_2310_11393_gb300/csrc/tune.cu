@@ -57,8 +57,18 @@ double trial(const pic_config& c, int steps, cudaStream_t st, pic_status* err)
     }
     pic_params p;
     pic_derive_params(&c, &p);
-    if ((c.beam == PIC_BEAM_LP || c.beam == PIC_BEAM_RP) && p.dt > 0) {
-        const long long k = std::max<long long>(0, std::llround(c.t_focus / p.dt) - steps);
+    // the clock is moved to the time the pulse is on the plasma, so that the incident field
+    // and the deposit do their full work in the trial
+    double t_on = -1.0;
+    if (c.beam == PIC_BEAM_LP || c.beam == PIC_BEAM_RP || c.beam == PIC_BEAM_GAUSS2D) {
+        t_on = c.t_focus;
+    } else if (c.beam == PIC_BEAM_PLANE && c.ppc > 0) {
+        // envelope centre (Gaussian: xi = t_focus; sin^2: xi = duration) at the slab centre
+        const double xc = 0.5 * (c.slab_lo[0] + c.slab_hi[0]) * c.dx;
+        t_on = xc - c.focus[0] + (c.envelope == PIC_ENV_GAUSS ? c.t_focus : c.duration);
+    }
+    if (t_on > 0 && p.dt > 0) {
+        const long long k = std::max<long long>(0, std::llround(t_on / p.dt) - steps);
         pic_set_step(s, k, st);
     }
     // untimed steps, then the faster of two timed stretches (the GPU is shared: a stretch
