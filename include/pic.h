@@ -287,6 +287,10 @@ typedef struct {
     int64_t memory_budget;   /* device bytes the resident simulations may use; 0: 80% of free memory */
     int32_t max_resident;    /* simulations on the device at once; 0: 256 */
     int32_t quantum;         /* steps advanced between admission rounds; 0: 50 */
+    int64_t fill_particles;  /* each quantum steps the resident simulations with the least
+                                remaining work (steps x electrons) first, adding more until
+                                this many electrons are in the batch (enough to fill the GPU);
+                                the others wait for the next quantum.  0: 6 000 000; < 0: all */
 } pic_serve_config;
 typedef struct {
     int32_t state;           /* 0 queued, 1 running, 2 done, -1 failed */

@@ -1,9 +1,12 @@
 // Continuous-batching request server (pic_serve_*): parameter-scan simulations arrive
 // at any time; a host scheduling thread admits queued requests whenever a resident
-// slot and device memory (estimated with pic_derive_params) are free, advances every
-// resident simulation together through the batched step for a quantum of steps (each
-// simulation stops exactly at its requested step count), retires finished ones with
-// their energies, and records submit / start / finish times on one clock.
+// slot and device memory (estimated with pic_derive_params) are free, and each quantum
+// advances a batch of resident simulations together through the batched step (each
+// simulation stops exactly at its requested step count).  The batch is chosen shortest
+// remaining work first (steps left x electrons) until it holds fill_particles electrons,
+// enough to fill the GPU: short requests finish early instead of sharing the device with
+// every long one to the end, and the device stays full.  Finished simulations retire
+// with their energies; submit / start / finish times are on one clock.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,6 +67,7 @@ void pic_server::run()
     int64_t used = 0;
     const int max_res = cfg.max_resident > 0 ? cfg.max_resident : 256;
     const int quantum = cfg.quantum > 0 ? cfg.quantum : 50;
+    const int64_t fill = cfg.fill_particles > 0 ? cfg.fill_particles : (cfg.fill_particles < 0 ? -1 : 6000000);
     for (;;) {
         // ---- admission (FIFO while memory and slots allow) ----
         std::vector<Request> admit;
@@ -105,22 +109,41 @@ void pic_server::run()
             used += q.bytes;
         }
         if (res.empty()) continue;
-        // ---- one quantum of batched steps ----
-        int64_t q = quantum;
-        for (const Resident& r : res) q = std::min(q, r.remaining);
-        std::vector<pic_sim*> list;
-        for (const Resident& r : res) list.push_back(r.sim);
+        // ---- the batch of this quantum: least remaining work first, until full ----
         std::vector<int64_t> alive(res.size());
         for (size_t i = 0; i < res.size(); ++i) {
             pic_info inf;
             alive[i] = pic_info_get(res[i].sim, &inf, st) == PIC_OK ? inf.n_alive : 0;
         }
+        std::vector<size_t> order(res.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+            return res[a].remaining * std::max<int64_t>(alive[a], 1) < res[b].remaining * std::max<int64_t>(alive[b], 1);
+        });
+        std::vector<char> chosen(res.size(), 0);
+        int64_t in_batch = 0;
+        for (size_t k = 0; k < order.size(); ++k) {
+            if (fill >= 0 && k > 0 && in_batch >= fill) break;
+            chosen[order[k]] = 1;
+            in_batch += alive[order[k]];
+        }
+        int64_t q = quantum;
+        std::vector<pic_sim*> list;
+        for (size_t i = 0; i < res.size(); ++i)
+            if (chosen[i]) {
+                q = std::min(q, res[i].remaining);
+                list.push_back(res[i].sim);
+            }
         pic_status e = q > 0 ? pic_batch_step(list.data(), (int)list.size(), (int)q, st) : PIC_OK;
         cudaStreamSynchronize(st);
         // ---- bookkeeping and retirement ----
         std::vector<Resident> keep;
         for (size_t i = 0; i < res.size(); ++i) {
             Resident r = res[i];
+            if (!chosen[i]) {
+                keep.push_back(r);
+                continue;
+            }
             r.remaining -= q;
             {
                 std::lock_guard<std::mutex> lk(mu);

@@ -59,7 +59,8 @@ class pic_allocator(Structure):
 
 
 class pic_serve_config(Structure):
-    _fields_ = [("memory_budget", c_int64), ("max_resident", c_int32), ("quantum", c_int32)]
+    _fields_ = [("memory_budget", c_int64), ("max_resident", c_int32), ("quantum", c_int32),
+                ("fill_particles", c_int64)]
 
 
 class pic_result(Structure):
@@ -251,8 +252,8 @@ def pic_batch_step(sims, n_steps: int, stream=0):
     return check(st, sims[0])
 
 
-def pic_serve_open(memory_budget=0, max_resident=0, quantum=0):
-    cfg = pic_serve_config(memory_budget, max_resident, quantum)
+def pic_serve_open(memory_budget=0, max_resident=0, quantum=0, fill_particles=0):
+    cfg = pic_serve_config(memory_budget, max_resident, quantum, fill_particles)
     h = c_void_p()
     check(load().pic_serve_open(byref(cfg), byref(h)))
     return h

@@ -72,7 +72,10 @@ def test_batch_against_the_oracle(P, orc):
         assert err < 1e-5, (w.name, err)
 
 
-def test_server_results_equal_alone(P):
+@pytest.mark.parametrize("fill", [0, 1])
+def test_server_results_equal_alone(P, fill):
+    """fill = 1: each quantum advances only the request with the least remaining work, so
+    the others wait; the results are the same either way."""
     ws = mix()
     steps = [40, 25, 60, 33]
     alone = []
@@ -81,7 +84,7 @@ def test_server_results_equal_alone(P):
         s.step(k)
         alone.append(s.energies())
         s.close()
-    srv = P.pic_serve_open(quantum=10)
+    srv = P.pic_serve_open(quantum=10, fill_particles=fill)
     tickets = []
     for w, k in zip(ws, steps):
         tickets.append(P.pic_serve_submit(srv, P.config_from(w), k))
