@@ -347,10 +347,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
             // window of four nodes starting one below the old support when sh = -1 and at it
             // otherwise.  S0 / DS: old shape / shape change on that window.  Along the
             // current's own axis the window's last partial sum is the total charge change,
-            // zero: three nodes carry that component.
+            // zero: one node fewer carries that component.  When no lane of the warp changes
+            // its nearest node along an axis (sh = 0 everywhere: most steps of most
+            // electrons), the window's fourth node is zero for every lane and the loops stop
+            // at three nodes on that axis (a warp-uniform bound).
             R S0[3][4], DS[3][4];
             int jw[3] = {0, 0, 0};
             R mv[3] = {R(0), R(0), R(0)};
+            bool cross[3] = {false, false, false};
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 mv[d] = dtdx * v[d];
@@ -363,6 +367,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                 shape2(d0, w0);
                 shape2(d1, w1);
                 const bool lo = sh < 0, hi = sh > 0;
+                cross[d] = sh != 0;
                 const R o0[4] = {lo ? R(0) : w0[0], lo ? w0[0] : w0[1], lo ? w0[1] : w0[2], lo ? w0[2] : R(0)};
                 const R n1[4] = {hi ? R(0) : w1[0], hi ? w1[0] : w1[1], hi ? w1[1] : w1[2], hi ? w1[2] : R(0)};
 #pragma unroll
@@ -372,6 +377,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                 }
                 jw[d] = c[d] + h0 - (lo ? 2 : 1) - T0[d] + hx[d];
             }
+            // window width per axis over the lanes running here (each lane's own vote is in
+            // its mask, so its width covers its own window whatever the warp's convergence)
+            const unsigned am = __activemask();
+            int nw[3] = {4, 4, 4};
+#pragma unroll
+            for (int d = 0; d < D; ++d) nw[d] = __any_sync(am, cross[d]) ? 4 : 3;
             R* Jx = Js;
             R* Jy = Js + bvol;
             R* Jz = Js + 2 * bvol;
@@ -381,11 +392,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                 R acc = R(0);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
+                    if (a >= nw[0] - 1) break;
                     acc += cw * DS[0][a];
                     sm_add(&Jx[jw[0] + a], acc);
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
+                    if (a >= nw[0]) break;
                     const R f = S0[0][a] + R(0.5) * DS[0][a];
                     sm_add(&Jy[jw[0] + a], -wt * v[1] * f);
                     sm_add(&Jz[jw[0] + a], -wt * v[2] * f);
@@ -393,73 +406,92 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
             } else if constexpr (D == 2) {
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
+                    if (b >= nw[1]) break;
                     const R fy = S0[1][b] + R(0.5) * DS[1][b];
                     R acc = R(0);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
+                        if (a >= nw[0] - 1) break;
                         acc += cw * DS[0][a] * fy;
                         sm_add(&Jx[(jw[1] + b) * bx + jw[0] + a], acc);
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
+                    if (a >= nw[0]) break;
                     const R fx = S0[0][a] + R(0.5) * DS[0][a];
                     R acc = R(0);
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
+                        if (b >= nw[1] - 1) break;
                         acc += cw * DS[1][b] * fx;
                         sm_add(&Jy[(jw[1] + b) * bx + jw[0] + a], acc);
                     }
                 }
                 const R qv = -wt * v[2];
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
+                for (int b = 0; b < 4; ++b) {
+                    if (b >= nw[1]) break;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
+                        if (a >= nw[0]) break;
                         const R wz = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
                                      R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
                         sm_add(&Jz[(jw[1] + b) * bx + jw[0] + a], qv * wz);
                     }
+                }
             } else {
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nw[2]) break;
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
+                        if (b >= nw[1]) break;
                         const R fyz = S0[1][b] * S0[2][cc] + R(0.5) * DS[1][b] * S0[2][cc] +
                                       R(0.5) * S0[1][b] * DS[2][cc] + third * DS[1][b] * DS[2][cc];
                         R acc = R(0);
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
+                            if (a >= nw[0] - 1) break;
                             acc += cw * DS[0][a] * fyz;
                             sm_add(&Jx[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
+                }
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nw[2]) break;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
+                        if (a >= nw[0]) break;
                         const R fxz = S0[0][a] * S0[2][cc] + R(0.5) * DS[0][a] * S0[2][cc] +
                                       R(0.5) * S0[0][a] * DS[2][cc] + third * DS[0][a] * DS[2][cc];
                         R acc = R(0);
 #pragma unroll
                         for (int b = 0; b < 3; ++b) {
+                            if (b >= nw[1] - 1) break;
                             acc += cw * DS[1][b] * fxz;
                             sm_add(&Jy[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
+                }
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
+                for (int b = 0; b < 4; ++b) {
+                    if (b >= nw[1]) break;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
+                        if (a >= nw[0]) break;
                         const R fxy = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
                                       R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
                         R acc = R(0);
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc) {
+                            if (cc >= nw[2] - 1) break;
                             acc += cw * DS[2][cc] * fxy;
                             sm_add(&Jz[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
+                }
             }
 
             // ---- move: carry the offset into the cell index; removal near the faces ----
