@@ -47,6 +47,8 @@ def parse():
                     help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
     ap.add_argument("--incident", default="particle", choices=["particle", "grid"],
                     help="incident field at every particle (Sec. 2) or on the Yee nodes, gathered")
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="steps between cell sorts within the tiles (<= 0: none)")
     ap.add_argument("--sims", type=int, default=256, help="batch: number of simulations")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (1/s)")
@@ -192,7 +194,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = workload(args.workload)
     tile = [int(v) for v in args.tile.split(",")] if args.tile else None
-    cfg = pic.config_from(w, tile=tile)
+    cfg = pic.config_from(w, tile=tile, sort_every=args.sort_every)
     stream = torch.cuda.current_stream(dev).cuda_stream
     alloc = pic.torch_allocator(local_rank)
     # tile and work-item size: measured by the autotuner (untimed set-up)
@@ -205,6 +207,7 @@ def run_ours(args, rank, world, local_rank):
     tune["push_tile"] = list(prm.tile)[: w.dim]
     tune["chunk"] = prm.chunk
     tune["field_solver_tile"] = list(prm.yee_tile)[: w.dim]
+    tune["cell_sort_every"] = prm.sort_every
     # warm-up: W steps on a throw-away instance (clocks, caches, graph, launch attributes)
     warm = pic.Simulation(cfg, allocator=alloc, stream=stream)
     warm.step(args.warmup)
@@ -291,7 +294,8 @@ def run_ours(args, rank, world, local_rank):
                       "cell_updates_per_s": cells * args.steps * world / t_max,
                       "l2": "inputs larger than L2 (device state %.2f GB > 129 MB)" % (info.params.device_bytes / 1e9),
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "tiles": tune},
-           "roofline": roof, "clocks": clk, "gpu_launches": (7 if w.incident_grid else 6) * args.steps, "e2e": e2e}
+           "roofline": roof, "clocks": clk, "gpu_launches": (7 if w.incident_grid else 6) * args.steps
+           + (2 * (args.steps // prm.sort_every) if prm.sort_every > 0 else 0), "e2e": e2e}
     return out
 
 

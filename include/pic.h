@@ -130,6 +130,13 @@ typedef struct {
                                 ppc; interpolation error O((k dx)^2); 0: at the particle (Sec. 2) */
     int32_t autotune_steps;  /* > 0: pic_init first runs pic_autotune with this many trial steps
                                 for a tile or chunk left at 0 (cached per shape) */
+    int32_t sort_every;      /* cell sort within the tiles (a layout choice, no counterpart in the
+                                paper): > 0: every sort_every-th step the tile re-sort also
+                                orders each tile's particles by cell (x fastest), so that a
+                                warp's lanes sit on neighbouring cells again; <= 0: never (the
+                                push measured no faster on sorted tiles).  Costs two arrays of
+                                one int per cell of the tiled grid.  Changes only the order of
+                                the particles (and with it the rounding order of the deposit). */
 } pic_config;
 
 /* Host-side derived quantities (pic_derive_params, pic_info). */
@@ -141,6 +148,7 @@ typedef struct {
     int32_t tile[3];         /* particle tile after autotuning */
     int32_t yee_tile[3];     /* field-solver tile (3D: x, y of a column and its segment in z) */
     int32_t chunk;           /* particles per push work item */
+    int32_t sort_every;      /* steps between cell sorts (0: none) */
 } pic_params;
 
 typedef struct {
@@ -195,7 +203,9 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
 pic_status pic_autotune(pic_config* cfg, int trial_steps, void* stream, double* ms_per_step);
 
 /* Advances n_steps >= 0 steps (one step: push + current deposition, particle re-sort,
- * field update).  Asynchronous on `stream` (graph replays). */
+ * field update).  Asynchronous on `stream` (graph replays).  Every sort_every-th step
+ * taken through pic_step or pic_profile_step (counted per sim from pic_init) replays the
+ * variant whose re-sort orders each tile's particles by cell. */
 pic_status pic_step(pic_sim* sim, int n_steps, void* stream);
 
 /* Advances n_steps steps like pic_step but launches the kernels one by one with CUDA
@@ -278,7 +288,9 @@ pic_status pic_eval_incident(pic_sim* sim, int64_t n, const double* pts, double*
 /* ---- batching: many independent simulations per launch --------------------------- */
 /* Advances every sim by n_steps: one persistent launch per phase over all their tiles
  * (sims grouped by dim and precision), the whole step captured as one CUDA graph that is
- * cached for this exact list.  All sims must live on the current device.  Asynchronous. */
+ * cached for this exact list.  All sims must live on the current device.  Asynchronous.
+ * The cell sort runs for every member that has one every k-th call step of this list,
+ * k the smallest sort_every among the members (counted per cached list). */
 pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, void* stream);
 
 /* ---- serving: continuous batching of a request stream ----------------------------- */

@@ -2,7 +2,8 @@
 // same dimension and precision form one launch group; each phase of the step (push +
 // deposit, tile scan, scatter, field solve, step end) is ONE persistent launch over the
 // (simulation, tile) work items of the whole group, pulled from a device counter.  The
-// step of all groups is captured once as a CUDA graph, cached per exact list of sims.
+// step of all groups is captured once as a CUDA graph (and once more with the cell sort),
+// cached per exact list of sims.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +26,10 @@ struct BatchEntry {
     std::vector<GroupRes> groups;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraph_t sort_graph = nullptr;     // the step whose re-sort orders the tiles by cell
+    cudaGraphExec_t sort_exec = nullptr;
+    int sort_every = 0;                   // smallest positive sort_every of the members (0: none)
+    int since_sort = 0;
     cudaStream_t cs = nullptr;
 };
 
@@ -35,6 +40,8 @@ void free_entry(BatchEntry* e)
 {
     if (e->exec) cudaGraphExecDestroy(e->exec);
     if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->sort_exec) cudaGraphExecDestroy(e->sort_exec);
+    if (e->sort_graph) cudaGraphDestroy(e->sort_graph);
     if (e->cs) cudaStreamDestroy(e->cs);
     for (auto& gr : e->groups)
         if (gr.mem) cudaFree(gr.mem);
@@ -104,6 +111,12 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         g.yee_smem = ysm;
         g.inc_any = 0;
         g.scan_blocks = n == 1 ? sims[mem[0]]->h.nscanblk : 0;
+        int maxtiles = 1;
+        for (int i : mem) {
+            maxtiles = std::max(maxtiles, sims[i]->h.nptiles);
+            const int k = sims[i]->sort_every;
+            if (k > 0 && (e->sort_every == 0 || k < e->sort_every)) e->sort_every = k;
+        }
         g.inc_segs = g.inc_rows = 1;
         for (int i : mem) {
             const pic_config& c = sims[i]->cfg;
@@ -118,29 +131,40 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         g.push_grid = (int)std::max<long long>(1, std::min<long long>(nch, (long long)bp * nsm));
         g.yee_grid = (int)std::max<long long>(1, std::min<long long>(nyw, (long long)byy * nsm));
         g.scatter_grid = (int)std::max<long long>(1, std::min<long long>(nch, (long long)bs * nsm));
+        g.cellscan_grid = std::max(1, std::min(maxtiles, 8 * nsm));
         e->groups.push_back(gr);
     }
-    if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamBeginCapture(e->cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess) {
         err = "batch capture could not start";
         free_entry(e);
         return PIC_ECUDA;
     }
-    for (auto& gr : e->groups) {
-        sff::launch_prefix(gr.g, e->cs);
-        sff::launch_incident_grid(gr.g, e->cs);
-        sff::launch_push(gr.g, e->cs);
-        sff::launch_scan(gr.g, e->cs);
-        sff::launch_scatter(gr.g, e->cs);
-        sff::launch_yee(gr.g, e->cs);
-        sff::launch_step_end(gr.g, e->cs);
-    }
-    cudaError_t ce = cudaStreamEndCapture(e->cs, &e->graph);
-    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e->exec, e->graph, 0);
-    if (ce != cudaSuccess) {
-        err = std::string("batch graph: ") + cudaGetErrorString(ce);
-        free_entry(e);
-        return PIC_ECUDA;
+    // the plain step, and (when a member sorts by cell) the cell-sort step
+    for (int v = 0; v < (e->sort_every > 0 ? 2 : 1); ++v) {
+        if (cudaStreamBeginCapture(e->cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            err = "batch capture could not start";
+            free_entry(e);
+            return PIC_ECUDA;
+        }
+        for (auto& gr : e->groups) {
+            sff::launch_prefix(gr.g, e->cs);
+            sff::launch_incident_grid(gr.g, e->cs);
+            sff::launch_push(gr.g, e->cs);
+            sff::launch_scan(gr.g, e->cs);
+            if (v == 1) sff::launch_scatter_sorted(gr.g, e->cs);
+            else sff::launch_scatter(gr.g, e->cs);
+            sff::launch_yee(gr.g, e->cs);
+            sff::launch_step_end(gr.g, e->cs);
+        }
+        cudaGraph_t* gp = v == 1 ? &e->sort_graph : &e->graph;
+        cudaGraphExec_t* xp = v == 1 ? &e->sort_exec : &e->exec;
+        cudaError_t ce = cudaStreamEndCapture(e->cs, gp);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(xp, *gp, 0);
+        if (ce != cudaSuccess) {
+            err = std::string("batch graph: ") + cudaGetErrorString(ce);
+            free_entry(e);
+            return PIC_ECUDA;
+        }
     }
     *out = e;
     return PIC_OK;
@@ -193,7 +217,12 @@ extern "C" pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, vo
     }
     cudaStream_t st = (cudaStream_t)stream;
     for (int i = 0; i < n_steps; ++i) {
-        cudaError_t ce = cudaGraphLaunch(e->exec, st);
+        bool sort = false;
+        if (e->sort_every > 0 && ++e->since_sort >= e->sort_every) {
+            e->since_sort = 0;
+            sort = true;
+        }
+        cudaError_t ce = cudaGraphLaunch(sort ? e->sort_exec : e->exec, st);
         if (ce != cudaSuccess) {
             key[0]->err = std::string("batch graph launch: ") + cudaGetErrorString(ce);
             return PIC_ECUDA;

@@ -155,6 +155,7 @@ struct Layout {
     int nptiles, nytiles;
     long long cap, max_exits, nslab;
     int chunk, max_chunks;
+    int tvol, sort_every;       // cells per particle tile; steps between cell sorts (0: none)
     size_t push_smem, yee_smem;
     size_t bytes;
 };
@@ -288,6 +289,12 @@ Layout make_layout(const pic_config* c)
     L.max_exits = c->max_exits > 0 ? c->max_exits : L.cap;
     L.chunk = c->chunk > 0 ? c->chunk : 2048;
     L.max_chunks = (int)(L.nptiles + (L.cap + L.chunk - 1) / L.chunk + 1);
+    L.tvol = L.pt[0] * L.pt[1] * L.pt[2];
+    // the cell-sort arrays are indexed by int: a tiled grid of 2^31 cells or more sorts by
+    // tile only (an explicit request is rejected)
+    const long long tcells = (long long)L.nptiles * L.tvol;
+    L.sort_every = std::max(0, c->sort_every);
+    if (tcells >= (1LL << 31)) L.sort_every = 0;
     const long long pbv = (long long)L.pb[0] * L.pb[1] * L.pb[2];
     const long long ybv = (long long)L.yb[0] * L.yb[1] * L.yb[2];
     const long long ytv = (long long)L.yt[0] * L.yt[1] * L.yt[2];
@@ -307,6 +314,7 @@ Layout make_layout(const pic_config* c)
     b += 4 * align256((size_t)(L.nptiles + 1) * 4) + 2 * align256((size_t)L.nptiles * 4);
     b += align256((size_t)((L.nptiles + 4095) / 4096) * 8) + align256(4);
     b += 2 * align256((size_t)L.max_chunks * 4);
+    if (L.sort_every > 0) b += 2 * align256((size_t)tcells * 4);
     b += align256((size_t)L.max_exits * EXIT_DOUBLES * 8);
     b += 2 * align256((size_t)L.natot * 8);
     b += align256((size_t)L.nytiles * sizeof(Work));
@@ -342,6 +350,9 @@ pic_status derive(const pic_config* c, pic_params* out, pic_sim* s)
         p.yee_tile[d] = L.yt[d];
     }
     p.chunk = L.chunk;
+    p.sort_every = L.sort_every;
+    if (c->sort_every > 0 && L.sort_every == 0)
+        return fail(s, PIC_EINVAL, "sort_every > 0 needs fewer than 2^31 cells in the tiled grid");
     *out = p;
     return PIC_OK;
 }
@@ -406,7 +417,8 @@ void dev_free(pic_sim* s, void* p)
     else s->alloc.free(p, s->alloc.ctx);
 }
 
-pic_status capture_step(pic_sim* s)
+// One step as a CUDA graph; `sorted`: the variant whose re-sort orders the tiles by cell.
+pic_status capture_step(pic_sim* s, bool sorted, GraphBundle* out)
 {
     cudaStream_t cs = s->cap_stream;
     CU_CHECK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -414,16 +426,26 @@ pic_status capture_step(pic_sim* s)
     launch_incident_grid(s->grp, cs);
     launch_push(s->grp, cs);
     launch_scan(s->grp, cs);
-    launch_scatter(s->grp, cs);
+    if (sorted) launch_scatter_sorted(s->grp, cs);
+    else launch_scatter(s->grp, cs);
     launch_yee(s->grp, cs);
     launch_step_end(s->grp, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (e != cudaSuccess) return fail(s, PIC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    s->step_graph.graph = g;
-    e = cudaGraphInstantiate(&s->step_graph.exec, g, 0);
+    out->graph = g;
+    e = cudaGraphInstantiate(&out->exec, g, 0);
     if (e != cudaSuccess) return fail(s, PIC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     return PIC_OK;
+}
+
+// true when the next step is a cell-sort step (advances the per-sim step count)
+bool next_is_sort(pic_sim* s)
+{
+    if (s->sort_every <= 0) return false;
+    if (++s->since_sort < s->sort_every) return false;
+    s->since_sort = 0;
+    return true;
 }
 
 pic_status read_state(pic_sim* s, DevState* out, cudaStream_t st)
@@ -568,6 +590,12 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.max_chunks = L.max_chunks;
     h.tcnt = (int*)A.take((size_t)L.nptiles * 4);
     h.tcur = (int*)A.take((size_t)L.nptiles * 4);
+    h.tvol = L.tvol;
+    if (L.sort_every > 0) {
+        h.ccnt = (int*)A.take((size_t)L.nptiles * L.tvol * 4);
+        h.ccur = (int*)A.take((size_t)L.nptiles * L.tvol * 4);
+    }
+    s->sort_every = L.sort_every;
     h.nscanblk = (L.nptiles + 4095) / 4096;
     h.scanflags = (unsigned long long*)A.take((size_t)h.nscanblk * 8);
     h.scanticket = (int*)A.take(4);
@@ -666,6 +694,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     INIT_CHECK(cudaMemsetAsync(h.coff[1], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcnt, 0, (size_t)L.nptiles * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcur, 0, (size_t)L.nptiles * 4, st));
+    if (h.ccnt) INIT_CHECK(cudaMemsetAsync(h.ccnt, 0, (size_t)L.nptiles * L.tvol * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.scanflags, 0, (size_t)h.nscanblk * 8, st));
     INIT_CHECK(cudaMemsetAsync(h.scanticket, 0, 4, st));
     INIT_CHECK(cudaMemsetAsync(s->d_counters, 0, 64, st));
@@ -727,13 +756,15 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     const int bs = std::max(1, scatter_blocks_per_sm(cfg->dim, cfg->precision));
     g.inc_any = h.incgrid;
     g.scan_blocks = h.nscanblk;
+    g.cellscan_grid = std::max(1, std::min(L.nptiles, 8 * nsm));
     g.inc_segs = (cfg->n[0] + 1 + 255) / 256;
     g.inc_rows = (cfg->dim > 1 ? cfg->n[1] + 1 : 1) * (cfg->dim > 2 ? cfg->n[2] + 1 : 1);
     g.push_grid = std::max(1, std::min(L.max_chunks, bp * nsm));
     g.yee_grid = std::max(1, std::min(L.nytiles, by * nsm));
     g.scatter_grid = std::max(1, std::min(L.max_chunks, bs * nsm));
     INIT_CHECK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-    if ((r = capture_step(s)) != PIC_OK) return cleanup(r);
+    if ((r = capture_step(s, false, &s->step_graph)) != PIC_OK) return cleanup(r);
+    if (s->sort_every > 0 && (r = capture_step(s, true, &s->sort_graph)) != PIC_OK) return cleanup(r);
 #undef INIT_CHECK
     *out = s;
     return PIC_OK;
@@ -744,7 +775,8 @@ pic_status pic_step(pic_sim* s, int n_steps, void* stream)
     if (!s) return fail(nullptr, PIC_EINVAL, "sim is NULL");
     if (n_steps < 0) return fail(s, PIC_EINVAL, "n_steps < 0");
     cudaStream_t st = (cudaStream_t)stream;
-    for (int i = 0; i < n_steps; ++i) CU_CHECK(s, cudaGraphLaunch(s->step_graph.exec, st));
+    for (int i = 0; i < n_steps; ++i)
+        CU_CHECK(s, cudaGraphLaunch(next_is_sort(s) ? s->sort_graph.exec : s->step_graph.exec, st));
     return PIC_OK;
 }
 
@@ -764,7 +796,8 @@ pic_status pic_profile_step(pic_sim* s, int n_steps, void* stream, double* secon
         cudaEventRecord(ev[1], st);
         launch_scan(s->grp, st);
         cudaEventRecord(ev[2], st);
-        launch_scatter(s->grp, st);
+        if (next_is_sort(s)) launch_scatter_sorted(s->grp, st);
+        else launch_scatter(s->grp, st);
         cudaEventRecord(ev[3], st);
         launch_yee(s->grp, st);
         cudaEventRecord(ev[4], st);
@@ -792,6 +825,8 @@ pic_status pic_destroy(pic_sim* s)
     batch_forget(s);
     if (s->step_graph.exec) cudaGraphExecDestroy(s->step_graph.exec);
     if (s->step_graph.graph) cudaGraphDestroy(s->step_graph.graph);
+    if (s->sort_graph.exec) cudaGraphExecDestroy(s->sort_graph.exec);
+    if (s->sort_graph.graph) cudaGraphDestroy(s->sort_graph.graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     dev_free(s, s->arena.base);
     delete s;

@@ -5,8 +5,9 @@
 //              atomic per nonzero cell (FP64); destination-tile counts are histogrammed in
 //              shared memory first (one global atomic per neighbour tile);
 //   k_scan     per-simulation exclusive scan of the destination-tile counts;
-//   k_scatter  stable-by-tile compaction into the other buffer set with warp-aggregated
-//              slot reservation;
+//   k_scatter  compaction by tile into the other buffer set with warp-aggregated slot
+//              reservation; every few steps, after k_cellcount / k_cellscan, by cell
+//              within the tile (the cell sort);
 //   k_step_end step counter and buffer parity.
 // Set-up kernels generate the seeded slab and sort arbitrary particle sets by tile.
 #include <cuda_runtime.h>
@@ -811,10 +812,35 @@ __device__ __forceinline__ int warp_reserve(int tile, int* cursors)
     return base + rank;
 }
 
+// Cell of c as an index of the tile-major cell arrays: tile * tvol + the cell's rank
+// within its tile, x fastest (the order the seeded slab is placed in).
+template <int D>
+__device__ __forceinline__ int cell_key(const SimDev& S, const int c[3], int* tile)
+{
+    int t = 0, r = 0;
+    const int q0 = c[0] / S.pt[0];
+    t = q0;
+    r = c[0] - q0 * S.pt[0];
+    if constexpr (D > 1) {
+        const int q1 = c[1] / S.pt[1];
+        t += S.npt[0] * q1;
+        r += S.pt[0] * (c[1] - q1 * S.pt[1]);
+    }
+    if constexpr (D > 2) {
+        const int q2 = c[2] / S.pt[2];
+        t += S.npt[0] * S.npt[1] * q2;
+        r += S.pt[0] * S.pt[1] * (c[2] - q2 * S.pt[2]);
+    }
+    *tile = t;
+    return t * S.tvol + r;
+}
+
 // Scatter of one chunk per work item: each warp reserves destination slots with one atomic
-// per distinct destination tile among its lanes (lanes going to the same tile write
-// consecutive slots).
-template <int D, typename R>
+// per distinct destination among its lanes (lanes going to the same destination write
+// consecutive slots).  The destination is the tile (slots after the tile's offset in the
+// order warps arrive) or, with SORT and a cell sort set up, the cell (slots after the
+// cell's offset within its tile, so that the tile comes out ordered by cell).
+template <int D, typename R, bool SORT>
 __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims, int nsims,
                                                  const int* __restrict__ gprefix, int* __restrict__ counter)
 {
@@ -829,19 +855,100 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
         const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
         const SimDev& S = sims[ck.sim];
         const int par = S.st->parity, np = 1 - par;
+        const bool by_cell = SORT && S.ccur != nullptr;
+        int* cur = by_cell ? S.ccur : S.tcur;
         for (int base = ck.p0; base < ck.p1; base += nth) {
             const int p = base + tid;
-            int t = -1;
+            int t = -1, key = -1;
             if (p < ck.p1) {
                 const unsigned cl = S.cell[par][p];
                 if (cl != DEAD) {
                     int c[3];
                     decode_cell<D>(S, cl, c);
-                    t = tile_of<D>(S, c);
+                    if (by_cell) {
+                        key = cell_key<D>(S, c, &t);
+                    } else {
+                        t = tile_of<D>(S, c);
+                        key = t;
+                    }
                 }
             }
-            const int slot = warp_reserve(t, S.tcur);
+            const int slot = warp_reserve(key, cur);
             if (t >= 0) copy_particle<D, R>(S, par, p, np, (long long)S.toff[np][t] + slot);
+        }
+    }
+}
+
+// Cell sort, first pass: per-cell counts of the pushed particles (buffer set `parity`, new
+// cells), one atomic per distinct cell among a warp's lanes.
+template <int D>
+__global__ void __launch_bounds__(256) k_cellcount(const SimDev* __restrict__ sims, int nsims,
+                                                   const int* __restrict__ gprefix, int* __restrict__ counter)
+{
+    __shared__ int s_item;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= gprefix[nsims]) break;
+        const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
+        const SimDev& S = sims[ck.sim];
+        if (S.ccnt == nullptr) continue;
+        const int par = S.st->parity;
+        for (int base = ck.p0; base < ck.p1; base += nth) {
+            const int p = base + tid;
+            int key = -1;
+            if (p < ck.p1) {
+                const unsigned cl = S.cell[par][p];
+                if (cl != DEAD) {
+                    int c[3], t;
+                    decode_cell<D>(S, cl, c);
+                    key = cell_key<D>(S, c, &t);
+                }
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&S.ccnt[key], __popc(peers));
+        }
+    }
+}
+
+// Cell sort, second pass: per tile (blocks stride over the tiles of simulation blockIdx.y),
+// exclusive scan of the cell counts into the write cursors; the counts are cleared for the
+// next sort.
+__global__ void __launch_bounds__(256) k_cellscan(const SimDev* __restrict__ sims)
+{
+    const SimDev& S = sims[blockIdx.y];
+    if (S.ccnt == nullptr) return;
+    __shared__ int s_warp[32];
+    __shared__ int s_total;
+    const int tid = threadIdx.x, tv = S.tvol;
+    for (int t = blockIdx.x; t < S.nptiles; t += gridDim.x) {
+        const long long base = (long long)t * tv;
+        int carry = 0;
+        for (int i0 = 0; i0 < tv; i0 += 4 * 256) {
+            int v[4], sum = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + 4 * tid + k;
+                v[k] = i < tv ? S.ccnt[base + i] : 0;
+                sum += v[k];
+            }
+            int run = carry + block_exclusive_scan(sum, s_warp);
+            if (tid == 255) s_total = run + sum;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + 4 * tid + k;
+                if (i < tv) {
+                    S.ccur[base + i] = run;
+                    S.ccnt[base + i] = 0;
+                }
+                run += v[k];
+            }
+            __syncthreads();
+            carry = s_total;
+            __syncthreads();
         }
     }
 }
@@ -1016,7 +1123,14 @@ static void push_t(const Group& g, cudaStream_t s)
 template <int D, typename R>
 static void scatter_t(const Group& g, cudaStream_t s)
 {
-    k_scatter<D, R><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
+    k_scatter<D, R, false><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
+}
+template <int D, typename R>
+static void cellsort_t(const Group& g, cudaStream_t s)
+{
+    k_cellcount<D><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 3);
+    k_cellscan<<<dim3((unsigned)g.cellscan_grid, (unsigned)g.nsims), 256, 0, s>>>(g.sims);
+    k_scatter<D, R, true><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
 }
 
 #define SFF_DISPATCH(dim, prec, FN, ...)                                 \
@@ -1034,6 +1148,7 @@ static void scatter_t(const Group& g, cudaStream_t s)
 
 void launch_push(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, push_t, g, s); }
 void launch_scatter(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, scatter_t, g, s); }
+void launch_scatter_sorted(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, cellsort_t, g, s); }
 void launch_scan(const Group& g, cudaStream_t s)
 {
     // a single simulation scans its tiles over several blocks; a batch, one block per member
@@ -1128,7 +1243,7 @@ int prepare_push(int dim, int prec, size_t smem)
 template <int D, typename R>
 static void attr_scatter(int* out)
 {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_scatter<D, R>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_scatter<D, R, false>, 256, 0);
 }
 int scatter_blocks_per_sm(int dim, int prec)
 {

@@ -102,6 +102,10 @@ struct alignas(128) SimDev {
     int max_chunks;
     int* tcnt;                // per-tile counts of the next step
     int* tcur;                // per-tile write cursors
+    int* ccnt;                // cell sort: per-cell counts [nptiles][tvol] (tile-major, x fastest
+                              // within a tile), zero between sorts; NULL without cell sort
+    int* ccur;                // cell sort: per-cell write cursors (offsets within the tile)
+    int tvol;                 // cells per particle tile
     unsigned long long* scanflags;   // multi-block tile scan: per block status | particles | chunks
     int* scanticket;          // multi-block tile scan: block order ticket
     int nscanblk;             // blocks of the multi-block tile scan (tiles / 4096, rounded up)

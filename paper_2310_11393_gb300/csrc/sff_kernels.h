@@ -34,6 +34,7 @@ struct Group {
     int push_grid, yee_grid, scatter_grid;
     int inc_any, inc_segs, inc_rows;   // incident field on the grid: any member, x segments, rows
     int scan_blocks;                   // single simulation: blocks of the multi-block tile scan
+    int cellscan_grid;                 // cell sort: blocks per simulation of the per-tile cell scan
 };
 
 // 3D field solver: columns of Y3_PX x Y3_PY points (x, y) marching along z through a
@@ -52,6 +53,9 @@ void launch_prefix(const Group& g, cudaStream_t s);
 void launch_push(const Group& g, cudaStream_t s);
 void launch_scan(const Group& g, cudaStream_t s);
 void launch_scatter(const Group& g, cudaStream_t s);
+// the re-sort of a cell-sort step: cell counts, per-tile cell scan, scatter by cell
+// (members without cell-sort arrays are scattered by tile)
+void launch_scatter_sorted(const Group& g, cudaStream_t s);
 void launch_yee(const Group& g, cudaStream_t s);
 void launch_step_end(const Group& g, cudaStream_t s);
 void launch_incident_grid(const Group& g, cudaStream_t s);

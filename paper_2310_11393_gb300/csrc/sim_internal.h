@@ -49,6 +49,9 @@ struct pic_sim {
     double* d_acc = nullptr;     // 8 doubles
     unsigned long long* d_bits = nullptr;
     GraphBundle step_graph;
+    GraphBundle sort_graph;      // the step whose re-sort orders the tiles by cell
+    int sort_every = 0;          // steps between cell sorts (0: none)
+    int since_sort = 0;          // steps through pic_step / pic_profile_step since the last one
     cudaStream_t cap_stream = nullptr;
     std::string err;
     long long nalloc_tot = 0;    // na_x*na_y*na_z

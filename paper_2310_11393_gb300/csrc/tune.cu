@@ -32,9 +32,9 @@ std::map<std::string, Choice> g_cache;
 std::string key_of(const pic_config* c)
 {
     char b[256];
-    snprintf(b, sizeof b, "%d|%d|%d,%d,%d|%d|%d|%d,%d,%d|%d,%d,%d|%d,%d,%d|%d", c->dim, c->precision, c->n[0], c->n[1],
-             c->n[2], c->ppc, c->beam, c->slab_lo[0], c->slab_lo[1], c->slab_lo[2], c->slab_hi[0], c->slab_hi[1],
-             c->slab_hi[2], c->tile[0], c->tile[1], c->tile[2], c->chunk);
+    snprintf(b, sizeof b, "%d|%d|%d,%d,%d|%d|%d|%d,%d,%d|%d,%d,%d|%d,%d,%d|%d|%d", c->dim, c->precision, c->n[0],
+             c->n[1], c->n[2], c->ppc, c->beam, c->slab_lo[0], c->slab_lo[1], c->slab_lo[2], c->slab_hi[0],
+             c->slab_hi[1], c->slab_hi[2], c->tile[0], c->tile[1], c->tile[2], c->chunk, c->sort_every);
     return b;
 }
 

@@ -35,14 +35,14 @@ class pic_config(Structure):
         ("n_e", c_double), ("ppc", c_int32), ("tile", c_int32 * 3), ("seed", c_uint64),
         ("max_particles", c_int64), ("max_exits", c_int64), ("chunk", c_int32), ("pusher", c_int32), ("profile", c_int32), ("prof_order", c_int32),
         ("prof_x0", c_double), ("prof_fwhm", c_double), ("prof_cut", c_double), ("tf_mode", c_int32),
-        ("incident_grid", c_int32), ("autotune_steps", c_int32),
+        ("incident_grid", c_int32), ("autotune_steps", c_int32), ("sort_every", c_int32),
     ]
 
 
 class pic_params(Structure):
     _fields_ = [("a", c_double), ("s", c_double), ("psi0", c_double), ("dt", c_double),
                 ("n_particles", c_int64), ("device_bytes", c_int64), ("tile", c_int32 * 3),
-                ("yee_tile", c_int32 * 3), ("chunk", c_int32)]
+                ("yee_tile", c_int32 * 3), ("chunk", c_int32), ("sort_every", c_int32)]
 
 
 class pic_info(Structure):
@@ -303,7 +303,8 @@ def torch_allocator(device=None):
     return a
 
 
-def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chunk=0, autotune_steps=0) -> pic_config:
+def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chunk=0, autotune_steps=0,
+                sort_every=0) -> pic_config:
     """pic_config for a workload description (attributes as synth.Workload)."""
     c = pic_config()
     c.dim = w.dim
@@ -337,6 +338,7 @@ def config_from(w, precision=None, tile=None, max_particles=0, max_exits=0, chun
     c.max_exits = max_exits
     c.chunk = chunk
     c.autotune_steps = autotune_steps
+    c.sort_every = sort_every
     c.pusher = getattr(w, "pusher", 0)
     c.profile = getattr(w, "profile", 0)
     c.prof_order = getattr(w, "prof_order", 12)

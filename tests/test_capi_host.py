@@ -117,3 +117,19 @@ def test_work_item_size_and_tuner_arguments(P):
     with pytest.raises(P.PicError) as e:
         P.pic_autotune(P.config_from(w), 0)
     assert e.value.status == P.PIC_EINVAL
+
+
+def test_cell_sort_cadence_is_resolved_and_sized(P):
+    """sort_every > 0 is kept, <= 0 turns the cell sort off; the cell sort's two int arrays
+    (one entry per cell of the tiled grid) are in the device footprint only when it is on."""
+    from _support import small_2d
+
+    w = small_2d()
+    got, size = {}, {}
+    for k in (0, -1, 5):
+        prm = P.pic_derive_params(P.config_from(w, tile=(16, 16), sort_every=k))
+        got[k], size[k] = prm.sort_every, prm.device_bytes
+    assert got == {0: 0, -1: 0, 5: 5}
+    tiled_cells = 96 * 80      # 6 x 5 tiles of 16 x 16
+    assert size[5] - size[-1] >= 2 * tiled_cells * 4
+    assert size[0] == size[-1]
