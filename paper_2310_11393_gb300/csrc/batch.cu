@@ -31,6 +31,8 @@ struct BatchEntry {
     int sort_every = 0;                   // smallest positive sort_every of the members (0: none)
     int since_sort = 0;
     cudaStream_t cs = nullptr;
+    cudaStream_t cs2 = nullptr;           // the field-solve branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 std::mutex g_mu;
@@ -43,6 +45,9 @@ void free_entry(BatchEntry* e)
     if (e->sort_exec) cudaGraphExecDestroy(e->sort_exec);
     if (e->sort_graph) cudaGraphDestroy(e->sort_graph);
     if (e->cs) cudaStreamDestroy(e->cs);
+    if (e->cs2) cudaStreamDestroy(e->cs2);
+    if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    if (e->ev_join) cudaEventDestroy(e->ev_join);
     for (auto& gr : e->groups)
         if (gr.mem) cudaFree(gr.mem);
     delete e;
@@ -134,7 +139,10 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         g.cellscan_grid = std::max(1, std::min(maxtiles, 8 * nsm));
         e->groups.push_back(gr);
     }
-    if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&e->cs2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         err = "batch capture could not start";
         free_entry(e);
         return PIC_ECUDA;
@@ -146,19 +154,28 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
             free_entry(e);
             return PIC_ECUDA;
         }
+        // per group: push, then the re-sort and the field solve concurrently, then the step end
+        cudaError_t ce = cudaSuccess;
         for (auto& gr : e->groups) {
             sff::launch_prefix(gr.g, e->cs);
             sff::launch_incident_grid(gr.g, e->cs);
             sff::launch_push(gr.g, e->cs);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e->ev_fork, e->cs);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->cs2, e->ev_fork, 0);
+            if (ce == cudaSuccess) {
+                sff::launch_yee(gr.g, e->cs2);
+                ce = cudaEventRecord(e->ev_join, e->cs2);
+            }
             sff::launch_scan(gr.g, e->cs);
             if (v == 1) sff::launch_scatter_sorted(gr.g, e->cs);
             else sff::launch_scatter(gr.g, e->cs);
-            sff::launch_yee(gr.g, e->cs);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->cs, e->ev_join, 0);
             sff::launch_step_end(gr.g, e->cs);
         }
         cudaGraph_t* gp = v == 1 ? &e->sort_graph : &e->graph;
         cudaGraphExec_t* xp = v == 1 ? &e->sort_exec : &e->exec;
-        cudaError_t ce = cudaStreamEndCapture(e->cs, gp);
+        const cudaError_t ec = cudaStreamEndCapture(e->cs, gp);
+        if (ce == cudaSuccess) ce = ec;
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(xp, *gp, 0);
         if (ce != cudaSuccess) {
             err = std::string("batch graph: ") + cudaGetErrorString(ce);

@@ -418,20 +418,33 @@ void dev_free(pic_sim* s, void* p)
 }
 
 // One step as a CUDA graph; `sorted`: the variant whose re-sort orders the tiles by cell.
+// After the push the graph forks: the particle re-sort (tile scan, scatter) and the field
+// solve touch disjoint data and run concurrently; the step end joins them.
 pic_status capture_step(pic_sim* s, bool sorted, GraphBundle* out)
 {
-    cudaStream_t cs = s->cap_stream;
+    cudaStream_t cs = s->cap_stream, cs2 = s->cap_stream2;
     CU_CHECK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     launch_prefix(s->grp, cs);
     launch_incident_grid(s->grp, cs);
     launch_push(s->grp, cs);
+    cudaError_t e = cudaEventRecord(s->ev_fork, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, s->ev_fork, 0);
+    if (e == cudaSuccess) {
+        launch_yee(s->grp, cs2);
+        e = cudaEventRecord(s->ev_join, cs2);
+    }
     launch_scan(s->grp, cs);
     if (sorted) launch_scatter_sorted(s->grp, cs);
     else launch_scatter(s->grp, cs);
-    launch_yee(s->grp, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, s->ev_join, 0);
     launch_step_end(s->grp, cs);
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = ec;
+    if (e != cudaSuccess && g) {
+        cudaGraphDestroy(g);
+        g = nullptr;
+    }
     if (e != cudaSuccess) return fail(s, PIC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     out->graph = g;
     e = cudaGraphInstantiate(&out->exec, g, 0);
@@ -763,6 +776,9 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     g.yee_grid = std::max(1, std::min(L.nytiles, by * nsm));
     g.scatter_grid = std::max(1, std::min(L.max_chunks, bs * nsm));
     INIT_CHECK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    INIT_CHECK(cudaStreamCreateWithFlags(&s->cap_stream2, cudaStreamNonBlocking));
+    INIT_CHECK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+    INIT_CHECK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
     if ((r = capture_step(s, false, &s->step_graph)) != PIC_OK) return cleanup(r);
     if (s->sort_every > 0 && (r = capture_step(s, true, &s->sort_graph)) != PIC_OK) return cleanup(r);
 #undef INIT_CHECK
@@ -828,6 +844,9 @@ pic_status pic_destroy(pic_sim* s)
     if (s->sort_graph.exec) cudaGraphExecDestroy(s->sort_graph.exec);
     if (s->sort_graph.graph) cudaGraphDestroy(s->sort_graph.graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->cap_stream2) cudaStreamDestroy(s->cap_stream2);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     dev_free(s, s->arena.base);
     delete s;
     return PIC_OK;

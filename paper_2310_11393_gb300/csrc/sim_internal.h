@@ -53,6 +53,8 @@ struct pic_sim {
     int sort_every = 0;          // steps between cell sorts (0: none)
     int since_sort = 0;          // steps through pic_step / pic_profile_step since the last one
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;   // the field-solve branch of the captured step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     long long nalloc_tot = 0;    // na_x*na_y*na_z
 };
