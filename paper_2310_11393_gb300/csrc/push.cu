@@ -835,6 +835,8 @@ __device__ __forceinline__ int cell_key(const SimDev& S, const int c[3], int* ti
     return t * S.tvol + r;
 }
 
+constexpr int SCATTER_NP = 2;
+
 // Scatter of one chunk per work item: each warp reserves destination slots with one atomic
 // per distinct destination among its lanes (lanes going to the same destination write
 // consecutive slots).  The destination is the tile (slots after the tile's offset in the
@@ -857,14 +859,31 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
         const int par = S.st->parity, np = 1 - par;
         const bool by_cell = SORT && S.ccur != nullptr;
         int* cur = by_cell ? S.ccur : S.tcur;
-        for (int base = ck.p0; base < ck.p1; base += nth) {
-            const int p = base + tid;
-            int t = -1, key = -1;
-            if (p < ck.p1) {
-                const unsigned cl = S.cell[par][p];
-                if (cl != DEAD) {
+        // SCATTER_NP particles per thread and round, all their loads issued before the slot
+        // reservations (more loads in flight per thread)
+        for (int base = ck.p0; base < ck.p1; base += SCATTER_NP * nth) {
+            unsigned cl[SCATTER_NP], id[SCATTER_NP];
+            R of[SCATTER_NP][D], mo[SCATTER_NP][3], wv[SCATTER_NP];
+#pragma unroll
+            for (int k = 0; k < SCATTER_NP; ++k) {
+                const int p = base + k * nth + tid;
+                cl[k] = DEAD;
+                if (p < ck.p1) {
+                    cl[k] = S.cell[par][p];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) of[k][d] = reinterpret_cast<const R*>(S.off[par][d])[p];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) mo[k][d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
+                    wv[k] = reinterpret_cast<const R*>(S.wgt[par])[p];
+                    id[k] = S.pid[par][p];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SCATTER_NP; ++k) {
+                int t = -1, key = -1;
+                if (cl[k] != DEAD) {
                     int c[3];
-                    decode_cell<D>(S, cl, c);
+                    decode_cell<D>(S, cl[k], c);
                     if (by_cell) {
                         key = cell_key<D>(S, c, &t);
                     } else {
@@ -872,9 +891,18 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
                         key = t;
                     }
                 }
+                const int slot = warp_reserve(key, cur);
+                if (t >= 0) {
+                    const long long q = (long long)S.toff[np][t] + slot;
+                    S.cell[np][q] = cl[k];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[np][d])[q] = of[k][d];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[np][d])[q] = mo[k][d];
+                    reinterpret_cast<R*>(S.wgt[np])[q] = wv[k];
+                    S.pid[np][q] = id[k];
+                }
             }
-            const int slot = warp_reserve(key, cur);
-            if (t >= 0) copy_particle<D, R>(S, par, p, np, (long long)S.toff[np][t] + slot);
         }
     }
 }
