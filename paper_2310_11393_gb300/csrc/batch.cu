@@ -22,6 +22,7 @@ struct GroupRes {
 };
 
 struct BatchEntry {
+    long long id = new_group_id();        // launch-group id of all groups of this list
     std::vector<pic_sim*> sims;
     std::vector<GroupRes> groups;
     cudaGraph_t graph = nullptr;
@@ -157,7 +158,6 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         // per group: push, then the re-sort and the field solve concurrently, then the step end
         cudaError_t ce = cudaSuccess;
         for (auto& gr : e->groups) {
-            sff::launch_prefix(gr.g, e->cs);
             sff::launch_incident_grid(gr.g, e->cs);
             sff::launch_push(gr.g, e->cs);
             if (ce == cudaSuccess) ce = cudaEventRecord(e->ev_fork, e->cs);
@@ -233,6 +233,14 @@ extern "C" pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, vo
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // the graph starts at the push: the chunks are numbered by the previous step's end when
+    // that step was this list's, else here
+    bool fresh = true;
+    for (pic_sim* s : key) fresh = fresh && s->prefix_group == e->id;
+    if (n_steps > 0 && !fresh) {
+        for (auto& gr : e->groups) sff::launch_prefix(gr.g, st);
+        for (pic_sim* s : key) s->prefix_group = e->id;
+    }
     for (int i = 0; i < n_steps; ++i) {
         bool sort = false;
         if (e->sort_every > 0 && ++e->since_sort >= e->sort_every) {

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -23,6 +24,12 @@
 #include "sim_internal.h"
 
 using namespace sff;
+
+long long new_group_id()
+{
+    static std::atomic<long long> next{1};
+    return next.fetch_add(1);
+}
 
 namespace {
 
@@ -419,12 +426,12 @@ void dev_free(pic_sim* s, void* p)
 
 // One step as a CUDA graph; `sorted`: the variant whose re-sort orders the tiles by cell.
 // After the push the graph forks: the particle re-sort (tile scan, scatter) and the field
-// solve touch disjoint data and run concurrently; the step end joins them.
+// solve touch disjoint data and run concurrently; the step end joins them and numbers the
+// next step's chunks (the graph starts at the push: see ensure_prefix).
 pic_status capture_step(pic_sim* s, bool sorted, GraphBundle* out)
 {
     cudaStream_t cs = s->cap_stream, cs2 = s->cap_stream2;
     CU_CHECK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    launch_prefix(s->grp, cs);
     launch_incident_grid(s->grp, cs);
     launch_push(s->grp, cs);
     cudaError_t e = cudaEventRecord(s->ev_fork, cs);
@@ -450,6 +457,15 @@ pic_status capture_step(pic_sim* s, bool sorted, GraphBundle* out)
     e = cudaGraphInstantiate(&out->exec, g, 0);
     if (e != cudaSuccess) return fail(s, PIC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     return PIC_OK;
+}
+
+// Before a step of the single-simulation group: number the chunks unless the last step of
+// this group did (k_step_end) and nothing changed the layout since.
+void ensure_prefix(pic_sim* s, cudaStream_t st)
+{
+    if (s->prefix_group == s->own_group_id) return;
+    launch_prefix(s->grp, st);
+    s->prefix_group = s->own_group_id;
 }
 
 // true when the next step is a cell-sort step (advances the per-sim step count)
@@ -561,6 +577,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
 
     pic_sim* s = new pic_sim();
     s->cfg = *cfg;
+    s->own_group_id = new_group_id();
     s->prm = prm;
     s->device = dev;
     if (alloc && alloc->alloc && alloc->free) {
@@ -791,6 +808,7 @@ pic_status pic_step(pic_sim* s, int n_steps, void* stream)
     if (!s) return fail(nullptr, PIC_EINVAL, "sim is NULL");
     if (n_steps < 0) return fail(s, PIC_EINVAL, "n_steps < 0");
     cudaStream_t st = (cudaStream_t)stream;
+    if (n_steps > 0) ensure_prefix(s, st);
     for (int i = 0; i < n_steps; ++i)
         CU_CHECK(s, cudaGraphLaunch(next_is_sort(s) ? s->sort_graph.exec : s->step_graph.exec, st));
     return PIC_OK;
@@ -804,8 +822,8 @@ pic_status pic_profile_step(pic_sim* s, int n_steps, void* stream, double* secon
     for (int i = 0; i < 6; ++i) CU_CHECK(s, cudaEventCreate(&ev[i]));
     for (int i = 0; i < 5; ++i) seconds[i] = 0.0;
     pic_status r = PIC_OK;
+    if (n_steps > 0) ensure_prefix(s, st);
     for (int k = 0; k < n_steps && r == PIC_OK; ++k) {
-        launch_prefix(s->grp, st);
         cudaEventRecord(ev[0], st);
         launch_incident_grid(s->grp, st);
         launch_push(s->grp, st);
@@ -937,6 +955,7 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
             CU_CHECK(s, cudaMemcpyAsync(s->h.mom[1][d], &mom[(size_t)d * n * es], n * es, cudaMemcpyHostToDevice, st));
         CU_CHECK(s, cudaMemcpyAsync(s->h.wgt[1], wt.data(), n * es, cudaMemcpyHostToDevice, st));
     }
+    s->prefix_group = 0;   // a new layout: the next step numbers its chunks first
     pic_status r = sort_linear_into_set0(s, n, st);
     if (r != PIC_OK) return r;
     // fields live in the set matching parity 0 now; keep the present field values

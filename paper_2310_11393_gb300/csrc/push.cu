@@ -981,15 +981,37 @@ __global__ void __launch_bounds__(256) k_cellscan(const SimDev* __restrict__ sim
     }
 }
 
-__global__ void k_step_end(const SimDev* __restrict__ sims, int nsims)
+// Last node of every step: step counter, particle count and buffer parity of every
+// simulation of the group, then the next step's chunk numbering and work counters (what
+// k_prefix does), so that a step of the same group needs no k_prefix of its own.
+__global__ void __launch_bounds__(1024) k_step_end(const SimDev* __restrict__ sims, int nsims,
+                                                   int* __restrict__ gprefix, int* __restrict__ counters)
 {
-    for (int i = threadIdx.x; i < nsims; i += blockDim.x) {
+    __shared__ int s_warp[32];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int per = (nsims + nth - 1) / nth;
+    const int i0 = min(nsims, tid * per), i1 = min(nsims, i0 + per);
+    int l = 0;
+    for (int i = i0; i < i1; ++i) {
         const SimDev& S = sims[i];
         DevState* st = S.st;
         const int np = 1 - st->parity;
         st->n_alive = S.toff[np][S.nptiles];
         st->parity = np;
         st->step += 1;
+        l += S.coff[np][S.nptiles];
+    }
+    int r = block_exclusive_scan(l, s_warp);
+    for (int i = i0; i < i1; ++i) {
+        gprefix[i] = r;
+        r += sims[i].coff[sims[i].st->parity][sims[i].nptiles];   // the parity this thread just set
+    }
+    if (tid == nth - 1) gprefix[nsims] = r;
+    if (tid < 4) counters[tid] = 0;
+    if (nsims == 1) {
+        const SimDev& S = sims[0];
+        for (int j = tid; j < S.nscanblk; j += nth) S.scanflags[j] = 0ull;
+        if (tid == 0) *S.scanticket = 0;
     }
 }
 
@@ -1184,7 +1206,10 @@ void launch_scan(const Group& g, cudaStream_t s)
     else k_scan<<<g.nsims, 1024, 0, s>>>(g.sims);
 }
 void launch_prefix(const Group& g, cudaStream_t s) { k_prefix<<<1, 1024, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters); }
-void launch_step_end(const Group& g, cudaStream_t s) { k_step_end<<<1, 256, 0, s>>>(g.sims, g.nsims); }
+void launch_step_end(const Group& g, cudaStream_t s)
+{
+    k_step_end<<<1, 1024, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters);
+}
 
 template <int D, typename R>
 static void incgrid_t(const Group& g, cudaStream_t s)

@@ -49,6 +49,11 @@ struct pic_sim {
     double* d_acc = nullptr;     // 8 doubles
     unsigned long long* d_bits = nullptr;
     GraphBundle step_graph;
+    // id of the launch group whose chunk numbering and work counters are set for this sim's
+    // current particle layout (each step ends by setting them for its own group; any other
+    // change of the layout clears it, and the next step of a group starts with k_prefix)
+    long long prefix_group = 0;
+    long long own_group_id = 0;  // id of the single-simulation group
     GraphBundle sort_graph;      // the step whose re-sort orders the tiles by cell
     int sort_every = 0;          // steps between cell sorts (0: none)
     int since_sort = 0;          // steps through pic_step / pic_profile_step since the last one
@@ -59,6 +64,9 @@ struct pic_sim {
     long long nalloc_tot = 0;    // na_x*na_y*na_z
 };
 
+
+// a fresh launch-group id (never 0; never reused in the process)
+long long new_group_id();
 
 // drop cached batch graphs that contain `s` (called by pic_destroy)
 void batch_forget(pic_sim* s);
