@@ -80,7 +80,10 @@ enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1, PIC_PUSHER_HC = 2 };
 enum {
     PIC_FLAG_TIMEOUT = 1u << 0,      /* an mbarrier wait exceeded its iteration bound */
     PIC_FLAG_CFL = 1u << 1,          /* a particle moved more than one cell in a step (removed) */
-    PIC_FLAG_EXIT_OVERFLOW = 1u << 2 /* exit records beyond max_exits were dropped */
+    PIC_FLAG_EXIT_OVERFLOW = 1u << 2, /* exit records beyond max_exits were dropped */
+    PIC_FLAG_CAPACITY = 1u << 3       /* a particle found no slot in its destination tile and was
+                                         dropped (the tile slack bounds the arrivals of a step,
+                                         so this marks a defect, not a configuration limit) */
 };
 
 typedef struct {
@@ -109,7 +112,8 @@ typedef struct {
     int32_t slab_hi[3];
     double n_e;              /* slab electron density (n_c) */
     int32_t ppc;             /* particles per slab cell (0: no slab) */
-    int32_t tile[3];         /* particle tile in cells (x a multiple of 4); 0: chosen by the autotuner */
+    int32_t tile[3];         /* particle tile in cells (2..248, x a multiple of 4); 0: chosen by the
+                                autotuner */
     uint64_t seed;           /* SplitMix64 seed of the slab positions */
     int64_t max_particles;   /* particle capacity; 0: slab count (pic_set_particles may need more) */
     int64_t max_exits;       /* exit-record capacity; 0: max_particles */
@@ -202,17 +206,19 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
  * pic_init error when no candidate could be created. */
 pic_status pic_autotune(pic_config* cfg, int trial_steps, void* stream, double* ms_per_step);
 
-/* Advances n_steps >= 0 steps (one step: push + current deposition, particle re-sort,
+/* Advances n_steps >= 0 steps (one step: push + current deposition with every particle
+ * placed straight into its destination tile of the other particle buffer set, tile scan,
  * field update).  Asynchronous on `stream` (graph replays).  Every sort_every-th step
  * taken through pic_step or pic_profile_step (counted per sim from pic_init) replays the
- * variant whose re-sort orders each tile's particles by cell. */
+ * variant that places each tile's particles in cell order. */
 pic_status pic_step(pic_sim* sim, int n_steps, void* stream);
 
 /* Advances n_steps steps like pic_step but launches the kernels one by one with CUDA
  * events recorded on `stream` between the phases, and returns in HOST seconds[5] the
  * summed device time of each phase: [0] push + deposit (with incident_grid: also the
- * evaluation of the incident field on the grid), [1] tile scan, [2] particle scatter,
- * [3] field solve, [4] step end.  Synchronous.  Used to time kernels live. */
+ * evaluation of the incident field on the grid), [1] tile scan, [2] cell-sort placement
+ * (zero on other steps), [3] field solve, [4] step end (with the next step's chunk
+ * numbering).  Synchronous.  Used to time kernels live. */
 pic_status pic_profile_step(pic_sim* sim, int n_steps, void* stream, double* seconds);
 
 /* Releases all device state; synchronises the simulation's work first.  NULL is a no-op. */

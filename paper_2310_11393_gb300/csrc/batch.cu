@@ -155,11 +155,12 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
             free_entry(e);
             return PIC_ECUDA;
         }
-        // per group: push, then the re-sort and the field solve concurrently, then the step end
+        // per group: push, then the tile scan (and cell sort) and the field solve
+        // concurrently, then the step end
         cudaError_t ce = cudaSuccess;
         for (auto& gr : e->groups) {
             sff::launch_incident_grid(gr.g, e->cs);
-            sff::launch_push(gr.g, e->cs);
+            sff::launch_push(gr.g, v == 1, e->cs);
             if (ce == cudaSuccess) ce = cudaEventRecord(e->ev_fork, e->cs);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->cs2, e->ev_fork, 0);
             if (ce == cudaSuccess) {
@@ -167,8 +168,7 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
                 ce = cudaEventRecord(e->ev_join, e->cs2);
             }
             sff::launch_scan(gr.g, e->cs);
-            if (v == 1) sff::launch_scatter_sorted(gr.g, e->cs);
-            else sff::launch_scatter(gr.g, e->cs);
+            if (v == 1) sff::launch_cell_sort(gr.g, e->cs);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->cs, e->ev_join, 0);
             sff::launch_step_end(gr.g, e->cs);
         }

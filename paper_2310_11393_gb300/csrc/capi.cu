@@ -161,6 +161,7 @@ struct Layout {
     long long sy, sz, sc, natot;
     int nptiles, nytiles;
     long long cap, max_exits, nslab;
+    long long slots;            // slots per particle buffer set: frame factor x cap
     int chunk, max_chunks;
     int tvol, sort_every;       // cells per particle tile; steps between cell sorts (0: none)
     size_t push_smem, yee_smem;
@@ -211,8 +212,8 @@ pic_status validate(const pic_config* c, pic_sim* s)
         if (!(c->n_e >= 0)) return fail(s, PIC_EINVAL, "n_e < 0");
     }
     for (int d = 0; d < c->dim; ++d)
-        if (c->tile[d] < 0 || (c->tile[d] > 0 && (c->tile[d] > 248 || (d == 0 && c->tile[d] % 4))))
-            return fail(s, PIC_EINVAL, "tile[%d] = %d invalid (x a multiple of 4, <= 248)", d, c->tile[d]);
+        if (c->tile[d] < 0 || (c->tile[d] > 0 && (c->tile[d] < 2 || c->tile[d] > 248 || (d == 0 && c->tile[d] % 4))))
+            return fail(s, PIC_EINVAL, "tile[%d] = %d invalid (2..248 cells, x a multiple of 4)", d, c->tile[d]);
     if (c->chunk < 0 || (c->chunk > 0 && (c->chunk % 256 || c->chunk > 16384)))
         return fail(s, PIC_EINVAL, "chunk = %d invalid (a multiple of 256, <= 16384)", c->chunk);
     if (c->autotune_steps < 0) return fail(s, PIC_EINVAL, "autotune_steps must be >= 0");
@@ -296,6 +297,11 @@ Layout make_layout(const pic_config* c)
     L.max_exits = c->max_exits > 0 ? c->max_exits : L.cap;
     L.chunk = c->chunk > 0 ? c->chunk : 2048;
     L.max_chunks = (int)(L.nptiles + (L.cap + L.chunk - 1) / L.chunk + 1);
+    // Every tile keeps slack for the particles within one cell outside it, the only ones a
+    // step can bring in (a move is under one cell per axis).  With tiles at least two cells
+    // wide a particle lies in the frames of at most 2^dim - 1 other tiles, so 2^dim slots
+    // per particle hold every tile's particles and slack.
+    L.slots = (1LL << c->dim) * L.cap;
     L.tvol = L.pt[0] * L.pt[1] * L.pt[2];
     // the cell-sort arrays are indexed by int: a tiled grid of 2^31 cells or more sorts by
     // tile only (an explicit request is rejected)
@@ -314,13 +320,13 @@ Layout make_layout(const pic_config* c)
     b += align256((size_t)L.ncomp * L.natot * L.es);
     const size_t per = 4 + (size_t)(c->dim + 4) * L.es + 4;
     for (int q = 0; q < 2; ++q) {
-        b += align256(L.cap * 4) * 2;                                  // cell, id
-        b += align256(L.cap * L.es) * (size_t)(c->dim + 4);            // off, mom, w
+        b += align256(L.slots * 4) * 2;                                // cell, id
+        b += align256(L.slots * L.es) * (size_t)(c->dim + 4);          // off, mom, w
     }
     (void)per;
-    b += 4 * align256((size_t)(L.nptiles + 1) * 4) + 2 * align256((size_t)L.nptiles * 4);
+    b += 4 * align256((size_t)(L.nptiles + 1) * 4) + 5 * align256((size_t)L.nptiles * 4);   // + tnum, fcnt
     b += align256((size_t)((L.nptiles + 4095) / 4096) * 8) + align256(4);
-    b += 2 * align256((size_t)L.max_chunks * 4);
+    b += 2 * align256((size_t)L.max_chunks * 4) + 2 * align256((size_t)L.max_chunks * 8);   // ctile, crange
     if (L.sort_every > 0) b += 2 * align256((size_t)tcells * 4);
     b += align256((size_t)L.max_exits * EXIT_DOUBLES * 8);
     b += 2 * align256((size_t)L.natot * 8);
@@ -350,6 +356,8 @@ pic_status derive(const pic_config* c, pic_params* out, pic_sim* s)
         p.a = a; p.s = sp; p.psi0 = psi0;
     }
     Layout L = make_layout(c);
+    if (L.slots >= (1LL << 31))
+        return fail(s, PIC_EINVAL, "particle capacity %lld x frame factor exceeds 2^31 slots", L.cap);
     p.n_particles = L.nslab;
     p.device_bytes = (int64_t)L.bytes;
     for (int d = 0; d < 3; ++d) {
@@ -424,16 +432,17 @@ void dev_free(pic_sim* s, void* p)
     else s->alloc.free(p, s->alloc.ctx);
 }
 
-// One step as a CUDA graph; `sorted`: the variant whose re-sort orders the tiles by cell.
-// After the push the graph forks: the particle re-sort (tile scan, scatter) and the field
-// solve touch disjoint data and run concurrently; the step end joins them and numbers the
-// next step's chunks (the graph starts at the push: see ensure_prefix).
+// One step as a CUDA graph; `sorted`: the variant whose particles are placed by cell.
+// After the push the graph forks: the tile scan (with, in the sorted variant, the cell-sort
+// placement) and the field solve touch disjoint data and run concurrently; the step end
+// joins them and numbers the next step's chunks (the graph starts at the push: see
+// ensure_prefix).
 pic_status capture_step(pic_sim* s, bool sorted, GraphBundle* out)
 {
     cudaStream_t cs = s->cap_stream, cs2 = s->cap_stream2;
     CU_CHECK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     launch_incident_grid(s->grp, cs);
-    launch_push(s->grp, cs);
+    launch_push(s->grp, sorted, cs);
     cudaError_t e = cudaEventRecord(s->ev_fork, cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, s->ev_fork, 0);
     if (e == cudaSuccess) {
@@ -441,8 +450,7 @@ pic_status capture_step(pic_sim* s, bool sorted, GraphBundle* out)
         e = cudaEventRecord(s->ev_join, cs2);
     }
     launch_scan(s->grp, cs);
-    if (sorted) launch_scatter_sorted(s->grp, cs);
-    else launch_scatter(s->grp, cs);
+    if (sorted) launch_cell_sort(s->grp, cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, s->ev_join, 0);
     launch_step_end(s->grp, cs);
     cudaGraph_t g = nullptr;
@@ -498,7 +506,7 @@ pic_status compute_rho_ion(pic_sim* s, cudaStream_t st)
     pic_status r = read_state(s, &ds, st);
     if (r != PIC_OK) return r;
     CU_CHECK(s, cudaMemsetAsync(s->h.scratch, 0, sizeof(double) * s->nalloc_tot, st));
-    launch_charge(s->d, s->cfg.dim, s->cfg.precision, ds.n_alive, s->h.scratch, st);
+    launch_charge(s->d, s->cfg.dim, s->cfg.precision, s->h.cap, s->h.scratch, st);
     std::vector<double> tmp(s->nalloc_tot);
     CU_CHECK(s, cudaMemcpyAsync(tmp.data(), s->h.scratch, sizeof(double) * s->nalloc_tot, cudaMemcpyDeviceToHost, st));
     CU_CHECK(s, cudaStreamSynchronize(st));
@@ -526,12 +534,18 @@ pic_status sort_linear_into_set0(pic_sim* s, long long n, cudaStream_t st)
     r = write_state(s, ds, st);
     if (r != PIC_OK) return r;
     CU_CHECK(s, cudaMemsetAsync(s->h.tcnt, 0, sizeof(int) * s->h.nptiles, st));
+    CU_CHECK(s, cudaMemsetAsync(s->h.fcnt, 0, sizeof(int) * s->h.nptiles, st));
+    CU_CHECK(s, cudaMemsetAsync(s->h.cell[0], 0xFF, (size_t)s->h.cap * 4, st));
+    CU_CHECK(s, cudaMemsetAsync(s->h.cell[1] + n, 0xFF, (size_t)(s->h.cap - n) * 4, st));
     launch_count_linear(s->d, s->cfg.dim, s->cfg.precision, n, st);
-    launch_scan_one(s->d, s->cfg.dim, s->cfg.precision, st);
+    launch_scan_one(s->d, 0, st);
     launch_sort_linear(s->d, s->cfg.dim, s->cfg.precision, n, st);
+    CU_CHECK(s, cudaMemsetAsync(s->h.tcur, 0, sizeof(int) * s->h.nptiles, st));
+    launch_next_slots(s->d, s->cfg.dim, s->cfg.precision, 0, n, st);
     CU_CHECK(s, cudaGetLastError());
     ds.parity = 0;
     ds.n_alive = (int)n;
+    ds.n_next = 0;
     return write_state(s, ds, st);
 }
 
@@ -601,11 +615,11 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.st = (DevState*)A.take(sizeof(DevState));
     h.F = A.take((size_t)L.ncomp * L.natot * L.es);
     for (int q = 0; q < 2; ++q) {
-        h.cell[q] = (unsigned*)A.take(L.cap * 4);
-        h.pid[q] = (unsigned*)A.take(L.cap * 4);
-        for (int d = 0; d < cfg->dim; ++d) h.off[q][d] = A.take(L.cap * L.es);
-        for (int d = 0; d < 3; ++d) h.mom[q][d] = A.take(L.cap * L.es);
-        h.wgt[q] = A.take(L.cap * L.es);
+        h.cell[q] = (unsigned*)A.take(L.slots * 4);
+        h.pid[q] = (unsigned*)A.take(L.slots * 4);
+        for (int d = 0; d < cfg->dim; ++d) h.off[q][d] = A.take(L.slots * L.es);
+        for (int d = 0; d < 3; ++d) h.mom[q][d] = A.take(L.slots * L.es);
+        h.wgt[q] = A.take(L.slots * L.es);
     }
     h.toff[0] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
     h.toff[1] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
@@ -613,6 +627,11 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.coff[1] = (int*)A.take((size_t)(L.nptiles + 1) * 4);
     h.ctile[0] = (int*)A.take((size_t)L.max_chunks * 4);
     h.ctile[1] = (int*)A.take((size_t)L.max_chunks * 4);
+    h.crange[0] = (int2*)A.take((size_t)L.max_chunks * 8);
+    h.crange[1] = (int2*)A.take((size_t)L.max_chunks * 8);
+    h.tnum[0] = (int*)A.take((size_t)L.nptiles * 4);
+    h.tnum[1] = (int*)A.take((size_t)L.nptiles * 4);
+    h.fcnt = (int*)A.take((size_t)L.nptiles * 4);
     h.chunk = L.chunk;
     h.lane_p = 8;
     if (cfg->ppc > 0)
@@ -626,6 +645,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
         h.ccur = (int*)A.take((size_t)L.nptiles * L.tvol * 4);
     }
     s->sort_every = L.sort_every;
+    s->pcap = L.cap;
     h.nscanblk = (L.nptiles + 4095) / 4096;
     h.scanflags = (unsigned long long*)A.take((size_t)h.nscanblk * 8);
     h.scanticket = (int*)A.take(4);
@@ -681,7 +701,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     h.s = prm.s;
     h.psi0 = prm.psi0;
     h.max_exits = L.max_exits;
-    h.cap = L.cap;
+    h.cap = L.slots;
     h.bcf = make_beam_consts<float>(h);
     h.bcd = make_beam_consts<double>(h);
     h.ycf = {(float)(prm.dt / cfg->dx), (float)(0.5 * prm.dt / cfg->dx), (float)prm.dt,
@@ -724,6 +744,10 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     INIT_CHECK(cudaMemsetAsync(h.coff[1], 0, (size_t)(L.nptiles + 1) * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcnt, 0, (size_t)L.nptiles * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.tcur, 0, (size_t)L.nptiles * 4, st));
+    INIT_CHECK(cudaMemsetAsync(h.fcnt, 0, (size_t)L.nptiles * 4, st));
+    INIT_CHECK(cudaMemsetAsync(h.tnum[0], 0, (size_t)L.nptiles * 4, st));
+    INIT_CHECK(cudaMemsetAsync(h.tnum[1], 0, (size_t)L.nptiles * 4, st));
+    for (int q = 0; q < 2; ++q) INIT_CHECK(cudaMemsetAsync(h.cell[q], 0xFF, (size_t)L.slots * 4, st));   // DEAD
     if (h.ccnt) INIT_CHECK(cudaMemsetAsync(h.ccnt, 0, (size_t)L.nptiles * L.tvol * 4, st));
     INIT_CHECK(cudaMemsetAsync(h.scanflags, 0, (size_t)h.nscanblk * 8, st));
     INIT_CHECK(cudaMemsetAsync(h.scanticket, 0, 4, st));
@@ -751,12 +775,15 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
         launch_gen_slab(s->d, cfg->dim, cfg->precision, L.nslab, cfg->ppc, lo, sn, cfg->seed,
                         cfg->n_e / cfg->ppc, st);
         INIT_CHECK(cudaGetLastError());
-        launch_scan_one(s->d, cfg->dim, cfg->precision, st);
+        launch_scan_one(s->d, 0, st);
         int hi[3] = {1, 1, 1};
         for (int d = 0; d < cfg->dim; ++d) hi[d] = cfg->slab_hi[d];
         launch_place_slab(s->d, cfg->dim, cfg->precision, L.nslab, cfg->ppc, lo, hi, st);
         INIT_CHECK(cudaGetLastError());
     }
+    // the first push's destination slots (set 1): tile counts plus frame counts
+    launch_next_slots(s->d, cfg->dim, cfg->precision, 0, L.nslab, st);
+    INIT_CHECK(cudaGetLastError());
     ds.parity = 0;
     ds.n_alive = (int)L.nslab;
     INIT_CHECK(cudaMemcpyAsync(h.st, &ds, sizeof ds, cudaMemcpyHostToDevice, st));
@@ -824,14 +851,14 @@ pic_status pic_profile_step(pic_sim* s, int n_steps, void* stream, double* secon
     pic_status r = PIC_OK;
     if (n_steps > 0) ensure_prefix(s, st);
     for (int k = 0; k < n_steps && r == PIC_OK; ++k) {
+        const bool sorted = next_is_sort(s);
         cudaEventRecord(ev[0], st);
         launch_incident_grid(s->grp, st);
-        launch_push(s->grp, st);
+        launch_push(s->grp, sorted, st);
         cudaEventRecord(ev[1], st);
         launch_scan(s->grp, st);
         cudaEventRecord(ev[2], st);
-        if (next_is_sort(s)) launch_scatter_sorted(s->grp, st);
-        else launch_scatter(s->grp, st);
+        if (sorted) launch_cell_sort(s->grp, st);
         cudaEventRecord(ev[3], st);
         launch_yee(s->grp, st);
         cudaEventRecord(ev[4], st);
@@ -900,8 +927,8 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
                              const int64_t* id, void* stream)
 {
     if (!s) return fail(nullptr, PIC_EINVAL, "sim is NULL");
-    if (n < 0 || n > s->h.cap) return fail(s, PIC_ECAPACITY, "%lld particles exceed the capacity %lld", (long long)n,
-                                           (long long)s->h.cap);
+    if (n < 0 || n > s->pcap) return fail(s, PIC_ECAPACITY, "%lld particles exceed the capacity %lld", (long long)n,
+                                          (long long)s->pcap);
     if (n > 0 && (!x || !u || !w || !id)) return fail(s, PIC_EINVAL, "NULL particle array");
     cudaStream_t st = (cudaStream_t)stream;
     const int D = s->cfg.dim, es = s->es;
@@ -1014,6 +1041,8 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
     pic_status r = read_state(s, &ds, st);
     if (r != PIC_OK) return r;
     if (ds.status & FLAG_TIMEOUT) return fail(s, PIC_ETIMEOUT, "a device wait timed out (status 0x%x)", ds.status);
+    if (ds.status & FLAG_CAPACITY)
+        return fail(s, PIC_ECAPACITY, "a particle found no slot in its destination tile (status 0x%x)", ds.status);
     const int D = s->cfg.dim;
     const long long nex = std::min<long long>(ds.n_exits, s->h.max_exits);
     double vol = 1.0;
@@ -1023,7 +1052,7 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
         if (bytes < 8 * sizeof(double)) return fail(s, PIC_ECAPACITY, "ENERGIES needs 64 bytes");
         CU_CHECK(s, cudaMemsetAsync(s->d_acc, 0, 4 * sizeof(double), st));
         launch_energy_fields(s->d, D, s->cfg.precision, s->h.n, s->d_acc, st);
-        launch_energy_particles(s->d, D, s->cfg.precision, ds.n_alive, nex, s->d_acc, st);
+        launch_energy_particles(s->d, D, s->cfg.precision, s->h.cap, nex, s->d_acc, st);
         CU_CHECK(s, cudaGetLastError());
         double acc[4];
         CU_CHECK(s, cudaMemcpyAsync(acc, s->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st));
@@ -1042,7 +1071,7 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
         if (bytes < sizeof(double)) return fail(s, PIC_ECAPACITY, "GAUSS needs 8 bytes");
         CU_CHECK(s, cudaMemsetAsync(s->h.scratch, 0, sizeof(double) * s->nalloc_tot, st));
         CU_CHECK(s, cudaMemsetAsync(s->d_bits, 0, 8, st));
-        launch_charge(s->d, D, s->cfg.precision, ds.n_alive, s->h.scratch, st);
+        launch_charge(s->d, D, s->cfg.precision, s->h.cap, s->h.scratch, st);
         launch_gauss(s->d, D, s->cfg.precision, s->h.n, s->h.scratch, s->d_bits, st);
         CU_CHECK(s, cudaGetLastError());
         unsigned long long bits;
@@ -1056,17 +1085,26 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
     case PIC_DIAG_PARTICLES: {
         const long long n = ds.n_alive;
         if (bytes < (size_t)n * 8 * sizeof(double)) return fail(s, PIC_ECAPACITY, "PARTICLES needs %lld bytes", n * 64);
-        const int q = ds.parity, es = s->es;
-        std::vector<unsigned> cell(n), pid(n);
-        std::vector<char> off((size_t)D * n * es), mom((size_t)3 * n * es), wt((size_t)n * es);
-        if (n > 0) {
-            CU_CHECK(s, cudaMemcpyAsync(cell.data(), s->h.cell[q], n * 4, cudaMemcpyDeviceToHost, st));
-            CU_CHECK(s, cudaMemcpyAsync(pid.data(), s->h.pid[q], n * 4, cudaMemcpyDeviceToHost, st));
+        const int q = ds.parity, es = s->es, nt = s->h.nptiles;
+        // the tiles' occupied slots of the current set, in tile order
+        std::vector<int> toff(nt + 1), tnum(nt);
+        CU_CHECK(s, cudaMemcpyAsync(toff.data(), s->h.toff[q], (nt + 1) * 4, cudaMemcpyDeviceToHost, st));
+        CU_CHECK(s, cudaMemcpyAsync(tnum.data(), s->h.tnum[q], nt * 4, cudaMemcpyDeviceToHost, st));
+        CU_CHECK(s, cudaStreamSynchronize(st));
+        const long long nu = std::min<long long>(toff[nt], s->h.cap);
+        long long tot = 0;
+        for (int t = 0; t < nt; ++t) tot += tnum[t];
+        if (tot != n) return fail(s, PIC_ECUDA, "tile counts (%lld) disagree with the particle count (%lld)", tot, n);
+        std::vector<unsigned> cell(nu), pid(nu);
+        std::vector<char> off((size_t)D * nu * es), mom((size_t)3 * nu * es), wt((size_t)nu * es);
+        if (nu > 0) {
+            CU_CHECK(s, cudaMemcpyAsync(cell.data(), s->h.cell[q], nu * 4, cudaMemcpyDeviceToHost, st));
+            CU_CHECK(s, cudaMemcpyAsync(pid.data(), s->h.pid[q], nu * 4, cudaMemcpyDeviceToHost, st));
             for (int d = 0; d < D; ++d)
-                CU_CHECK(s, cudaMemcpyAsync(&off[(size_t)d * n * es], s->h.off[q][d], n * es, cudaMemcpyDeviceToHost, st));
+                CU_CHECK(s, cudaMemcpyAsync(&off[(size_t)d * nu * es], s->h.off[q][d], nu * es, cudaMemcpyDeviceToHost, st));
             for (int d = 0; d < 3; ++d)
-                CU_CHECK(s, cudaMemcpyAsync(&mom[(size_t)d * n * es], s->h.mom[q][d], n * es, cudaMemcpyDeviceToHost, st));
-            CU_CHECK(s, cudaMemcpyAsync(wt.data(), s->h.wgt[q], n * es, cudaMemcpyDeviceToHost, st));
+                CU_CHECK(s, cudaMemcpyAsync(&mom[(size_t)d * nu * es], s->h.mom[q][d], nu * es, cudaMemcpyDeviceToHost, st));
+            CU_CHECK(s, cudaMemcpyAsync(wt.data(), s->h.wgt[q], nu * es, cudaMemcpyDeviceToHost, st));
         }
         CU_CHECK(s, cudaStreamSynchronize(st));
         auto rd = [&](const std::vector<char>& v, size_t idx) {
@@ -1080,18 +1118,23 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
             return x;
         };
         double* o = (double*)host_out;
-        for (long long p = 0; p < n; ++p) {
-            const unsigned cl = cell[p];
-            int c[3];
-            c[0] = (int)(cl & ((1u << s->h.cb[0]) - 1u));
-            c[1] = D > 1 ? (int)((cl >> s->h.cb[0]) & ((1u << s->h.cb[1]) - 1u)) : 0;
-            c[2] = D > 2 ? (int)(cl >> (s->h.cb[0] + s->h.cb[1])) : 0;
-            for (int d = 0; d < 3; ++d)
-                o[8 * p + d] = d < D ? ((double)c[d] + rd(off, (size_t)d * n + p)) * s->cfg.dx : 0.0;
-            for (int d = 0; d < 3; ++d) o[8 * p + 3 + d] = rd(mom, (size_t)d * n + p);
-            o[8 * p + 6] = rd(wt, p);
-            o[8 * p + 7] = (double)pid[p];
+        long long k = 0;
+        for (int t = 0; t < nt; ++t) {
+            const long long p1 = std::min<long long>((long long)toff[t] + tnum[t], nu);
+            for (long long p = toff[t]; p < p1; ++p, ++k) {
+                const unsigned cl = cell[p];
+                int c[3];
+                c[0] = (int)(cl & ((1u << s->h.cb[0]) - 1u));
+                c[1] = D > 1 ? (int)((cl >> s->h.cb[0]) & ((1u << s->h.cb[1]) - 1u)) : 0;
+                c[2] = D > 2 ? (int)(cl >> (s->h.cb[0] + s->h.cb[1])) : 0;
+                for (int d = 0; d < 3; ++d)
+                    o[8 * k + d] = d < D ? ((double)c[d] + rd(off, (size_t)d * nu + p)) * s->cfg.dx : 0.0;
+                for (int d = 0; d < 3; ++d) o[8 * k + 3 + d] = rd(mom, (size_t)d * nu + p);
+                o[8 * k + 6] = rd(wt, p);
+                o[8 * k + 7] = (double)pid[p];
+            }
         }
+        if (k != n) return fail(s, PIC_ECUDA, "tile slots hold %lld particles, expected %lld", k, n);
         return PIC_OK;
     }
     case PIC_DIAG_EXITS: {
@@ -1160,7 +1203,7 @@ pic_status pic_histogram(pic_sim* s, int n_e, double e_max, int n_a, double* hos
     const size_t nb = (size_t)n_e * n_a;
     if (nb > (size_t)s->nalloc_tot) return fail(s, PIC_ECAPACITY, "too many bins");
     CU_CHECK(s, cudaMemsetAsync(s->h.scratch, 0, nb * 8, st));
-    launch_histogram(s->d, s->cfg.dim, s->cfg.precision, ds.n_alive, std::min<long long>(ds.n_exits, s->h.max_exits),
+    launch_histogram(s->d, s->cfg.dim, s->cfg.precision, s->h.cap, std::min<long long>(ds.n_exits, s->h.max_exits),
                      n_e, e_max, n_a, s->h.scratch, st);
     CU_CHECK(s, cudaGetLastError());
     CU_CHECK(s, cudaMemcpyAsync(host_out, s->h.scratch, nb * 8, cudaMemcpyDeviceToHost, st));

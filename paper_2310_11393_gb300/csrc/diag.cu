@@ -25,6 +25,30 @@ __device__ __forceinline__ void decode_cell_d(const SimDev& S, unsigned cl, int 
     if constexpr (D > 2) c[2] = (int)(cl >> (S.cb[0] + S.cb[1]));
 }
 
+// Slot p of buffer set par holds a particle: slots after a tile's particles hold DEAD or
+// stale records of earlier steps, whose cell puts them outside their tile's occupied slots.
+template <int D>
+__device__ __forceinline__ bool slot_live(const SimDev& S, int par, long long p)
+{
+    const unsigned cl = S.cell[par][p];
+    if (cl == DEAD) return false;
+    int c[3];
+    decode_cell_d<D>(S, cl, c);
+    int t = 0, mul = 1;
+    for (int d = 0; d < D; ++d) {
+        if (c[d] >= S.n[d]) return false;
+        t += (c[d] / S.pt[d]) * mul;
+        mul *= S.npt[d];
+    }
+    return (unsigned long long)(p - S.toff[par][t]) < (unsigned long long)S.tnum[par][t];
+}
+
+// end of the occupied slot range of buffer set par (n: slots of a set)
+__device__ __forceinline__ long long slots_used(const SimDev& S, int par, long long n)
+{
+    return min(n, (long long)S.toff[par][S.nptiles]);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -32,14 +56,17 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// charge density rho_e = -sum w S(x - x_node) on the primal nodes (array coordinates)
+// charge density rho_e = -sum w S(x - x_node) on the primal nodes (array coordinates);
+// n: slots of a buffer set (as for the other particle diagnostics)
 template <int D, typename R>
 __global__ void k_charge(const SimDev* __restrict__ sim, long long n, double* __restrict__ rho)
 {
     const SimDev& S = *sim;
     const int par = S.st->parity;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+    const long long nu = slots_used(S, par, n);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nu;
          p += (long long)gridDim.x * blockDim.x) {
+        if (!slot_live<D>(S, par, p)) continue;
         int c[3];
         decode_cell_d<D>(S, S.cell[par][p], c);
         double w[3][3];
@@ -151,8 +178,10 @@ __global__ void k_energy_particles(const SimDev* __restrict__ sim, long long n, 
     const SimDev& S = *sim;
     const int par = S.st->parity;
     double ka = 0.0, ke = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+    const long long nu = slots_used(S, par, n);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nu;
          p += (long long)gridDim.x * blockDim.x) {
+        if (!slot_live<D>(S, par, p)) continue;
         double u2 = 0.0;
         for (int d = 0; d < 3; ++d) {
             const double u = (double)reinterpret_cast<const R*>(S.mom[par][d])[p];
@@ -193,8 +222,10 @@ __global__ void k_histogram(const SimDev* __restrict__ sim, long long n, long lo
 {
     const SimDev& S = *sim;
     const int par = S.st->parity;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+    const long long nu = slots_used(S, par, n);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nu;
          p += (long long)gridDim.x * blockDim.x) {
+        if (!slot_live<D>(S, par, p)) continue;
         hist_add(bins, (double)reinterpret_cast<const R*>(S.mom[par][0])[p],
                  (double)reinterpret_cast<const R*>(S.mom[par][1])[p],
                  (double)reinterpret_cast<const R*>(S.mom[par][2])[p], (double)reinterpret_cast<const R*>(S.wgt[par])[p],
@@ -365,7 +396,7 @@ extern "C" pic_status pic_histogram_static(pic_sim* s, int n_e, double e_max, in
     const size_t nb = (size_t)n_e * n_a;
     if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, nb * sizeof(double), st);
     if (e == cudaSuccess) {
-        sff::launch_histogram(s->d, s->cfg.dim, s->cfg.precision, ds.n_alive,
+        sff::launch_histogram(s->d, s->cfg.dim, s->cfg.precision, s->h.cap,
                               std::min<long long>(ds.n_exits, s->h.max_exits), n_e, e_max, n_a, bins, st);
         e = cudaGetLastError();
     }

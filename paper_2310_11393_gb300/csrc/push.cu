@@ -97,8 +97,8 @@ __device__ __forceinline__ void sm_add(double* a, double v)
     if (v != 0.0) atomicAdd(a, v);
 }
 
-// Global chunk k of a launch group -> simulation, tile and particle range.  Chunks are
-// numbered per simulation by the tile scan (coff / ctile) and across the group by gprefix.
+// Global chunk k of a launch group -> simulation, tile and particle slots.  Chunks are
+// numbered per simulation by the tile scan (ctile / crange) and across the group by gprefix.
 struct ChunkRef {
     int sim, tile, p0, p1;
 };
@@ -114,14 +114,27 @@ __device__ __forceinline__ ChunkRef chunk_of(const SimDev* __restrict__ sims, in
     const SimDev& S = sims[lo];
     const int par = S.st->parity;
     const int j = k - gprefix[lo];
-    const int t = S.ctile[par][j];
-    const int c = j - S.coff[par][t];
+    const int2 pr = S.crange[par][j];
     ChunkRef r;
     r.sim = lo;
-    r.tile = t;
-    r.p0 = S.toff[par][t] + c * S.chunk;
-    r.p1 = min(r.p0 + S.chunk, S.toff[par][t + 1]);
+    r.tile = S.ctile[par][j];
+    r.p0 = pr.x;
+    r.p1 = pr.y;
     return r;
+}
+
+// Reserve destination slots for a warp's particles (tile < 0: nothing to place); every lane of
+// the warp must call it.
+__device__ __forceinline__ int warp_reserve(int tile, int* cursors)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, tile);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (tile >= 0 && lane == leader) base = atomicAdd(&cursors[tile], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + rank;
 }
 
 // ---- momentum updates; h = q dt / 2 (q = -1, m = 1, c = 1) ----------------------------
@@ -195,14 +208,55 @@ __device__ __forceinline__ void higuera_cary_update(R u[3], const R E[3], const 
     for (int d = 0; d < 3; ++d) u[d] = R(2) * ub[d] - um[d] + h * E[d];
 }
 
+// Frame count of a particle that lands in cell cn of the tile at offset rel (-1, 0, 1 per
+// axis) from the work item's tile T0: every neighbour of that tile whose one-cell frame
+// holds cn (cn on the tile's first cell along an axis: the neighbour below; on its last:
+// the neighbour above; and their combinations along several axes) gets one count, in a
+// shared-memory histogram over tile offsets -2..2 per axis from the work item's tile.
+// Tiles are at least two cells wide, so a cell is first or last along an axis, not both.
+template <int D>
+__device__ __forceinline__ void frame_count(const SimDev& S, const int cn[3], const int T0[3], const int rel[3],
+                                            int* s_frame)
+{
+    int f[3] = {0, 0, 0}, base = 0;
+    bool any = false;
+    constexpr int W[3] = {1, 5, 25};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int l = cn[d] - (T0[d] + rel[d] * S.pt[d]);
+        f[d] = l == 0 ? -1 : (l == S.pt[d] - 1 ? 1 : 0);
+        any = any || f[d] != 0;
+        base += (rel[d] + 2) * W[d];
+    }
+    if (!any) return;
+#pragma unroll
+    for (int m = 1; m < (1 << D); ++m) {
+        int idx = base;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if ((m >> d) & 1) {
+                ok = ok && f[d] != 0;
+                idx += f[d] * W[d];
+            }
+        if (ok) atomicAdd(&s_frame[idx], 1);
+    }
+}
+
+// `sorting`: this step's re-sort orders the tiles by cell; then the simulations that have a
+// cell sort are pushed in place (k_scatter places them) and the others straight into the
+// other buffer set like every step.
 template <int D, typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_push(const SimDev* __restrict__ sims, int nsims,
-                                              const int* __restrict__ gprefix, int* __restrict__ counter)
+                                              const int* __restrict__ gprefix, int* __restrict__ counter,
+                                              int sorting)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item;
     __shared__ int s_hist[27];
+    constexpr int NFR = D == 1 ? 5 : (D == 2 ? 25 : 125);
+    __shared__ int s_frame[NFR];
     __shared__ PhaseRef<R> s_pref;
     const int tid = threadIdx.x, nth = blockDim.x;
     if (tid == 0) {
@@ -220,8 +274,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
         const SimDev& S = sims[ck.sim];
         DevState* st = S.st;
-        const int par = st->parity;
+        const int par = st->parity, np = 1 - par;
         const int p0 = ck.p0, p1 = ck.p1;
+        const bool direct = !(sorting && S.ccnt != nullptr);
 
         int tc[3] = {0, 0, 0};
         {
@@ -251,6 +306,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         }
         for (int i = tid; i < 3 * bvol; i += nth) Js[i] = R(0);
         if (tid < 27) s_hist[tid] = 0;
+        for (int i = tid; i < NFR; i += nth) s_frame[i] = 0;
         const bool ok = mbar_wait_bounded(&bar, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
@@ -287,17 +343,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         }
         for (int rb = p0; rb < p1; rb += nth) {
             const int p = rb + q;
-            if (p >= p1) continue;
+            // what the placement below needs: new cell (DEAD: removed or no particle),
+            // destination tile, offsets, momentum, weight
+            unsigned ncl = DEAD;
+            int tdst = -1;
+            R on[3] = {R(0), R(0), R(0)}, u[3] = {R(0), R(0), R(0)}, wt = R(0);
+            if (p < p1) {
             const unsigned cl = S.cell[par][p];
             int c[3];
             decode_cell<D>(S, cl, c);
             R o[3] = {R(0), R(0), R(0)};
 #pragma unroll
             for (int d = 0; d < D; ++d) o[d] = reinterpret_cast<const R*>(S.off[par][d])[p];
-            R u[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) u[d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
-            const R wt = reinterpret_cast<const R*>(S.wgt[par])[p];
+            wt = reinterpret_cast<const R*>(S.wgt[par])[p];
 
             // ---- gather of the scattered field (order-2 shapes on the Yee stagger) ----
             R Wp[3][3], Wd[3][3];
@@ -497,7 +557,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
 
             // ---- move: carry the offset into the cell index; removal near the faces ----
             int cn[3] = {c[0], c[1], c[2]};
-            R on[3] = {R(0), R(0), R(0)};
             bool dead = false;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
@@ -513,7 +572,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                 on[d] = r;
                 if (cn[d] < S.margin || cn[d] >= S.n[d] - S.margin) dead = true;
             }
-            unsigned ncl = DEAD;
             if (dead) {
                 const int slot = atomicAdd(&st->n_exits, 1);
                 if (slot < S.max_exits) {
@@ -529,20 +587,49 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                 }
             } else {
                 // destination tile relative to this one (a move is under one cell per axis)
-                int hidx = 0, mul = 1;
+                int hidx = 0, mul = 1, tg = 0, tmul = 1;
+                int rel[3] = {0, 0, 0};
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    hidx += (cn[d] < T0[d] ? 0 : (cn[d] >= T0[d] + S.pt[d] ? 2 : 1)) * mul;
+                    rel[d] = cn[d] < T0[d] ? -1 : (cn[d] >= T0[d] + S.pt[d] ? 1 : 0);
+                    hidx += (rel[d] + 1) * mul;
                     mul *= 3;
+                    tg += (tc[d] + rel[d]) * tmul;
+                    tmul *= S.npt[d];
                 }
                 atomicAdd(&s_hist[hidx], 1);
+                frame_count<D>(S, cn, T0, rel, s_frame);
                 ncl = encode_cell<D>(S, cn);
+                tdst = tg;
             }
-            S.cell[par][p] = ncl;
+            if (!direct) {
+                S.cell[par][p] = ncl;
 #pragma unroll
-            for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
+                for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
+                for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
+            }
+            }
+            // ---- placement into the destination tile's slots of the other buffer set (all
+            // lanes of the warp take part in the reservation) ----
+            if (direct) {
+                const int slot = warp_reserve(tdst, S.tcur);
+                if (tdst >= 0) {
+                    const long long q0 = S.toff[np][tdst];
+                    if (slot < S.toff[np][tdst + 1] - q0) {
+                        const long long qd = q0 + slot;
+                        S.cell[np][qd] = ncl;
+#pragma unroll
+                        for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[np][d])[qd] = on[d];
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[np][d])[qd] = u[d];
+                        reinterpret_cast<R*>(S.wgt[np])[qd] = wt;
+                        S.pid[np][qd] = S.pid[par][p];
+                    } else {
+                        atomicOr(&st->status, (unsigned)FLAG_CAPACITY);   // cannot happen: the slack bounds the arrivals
+                    }
+                }
+            }
         }
         __syncthreads();
 
@@ -579,6 +666,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
             }
             atomicAdd(&S.tcnt[nt], s_hist[tid]);
         }
+        for (int i = tid; i < NFR; i += nth) {
+            const int v = s_frame[i];
+            if (v > 0) {
+                int h = i, nt = 0, mul = 1;
+                bool in = true;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int tcd = tc[d] + h % 5 - 2;
+                    h /= 5;
+                    in = in && tcd >= 0 && tcd < S.npt[d];
+                    nt += tcd * mul;
+                    mul *= S.npt[d];
+                }
+                if (in) atomicAdd(&S.fcnt[nt], v);
+            }
+        }
         if constexpr (sizeof(R) == 4) {
             if (tid == 0) bulk_wait_read0();
         }
@@ -614,41 +717,63 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp)
     return r;
 }
 
-// Exclusive scan of the destination counts of one simulation (one block of 1024 threads):
-// tile offsets toff, chunk offsets coff (ceil(count / chunk) chunks per tile) and the
-// chunk -> tile map of buffer set `outpar`; clears the counts and cursors.
-__device__ void scan_counts(const SimDev& S, int outpar)
+// Chunks of tile t of buffer set q holding c particles from slot base: ctile / crange
+// entries from chunk index rc on.
+__device__ __forceinline__ void write_chunks(const SimDev& S, int q, int t, int base, int c, int rc)
+{
+    const int nc = (c + S.chunk - 1) / S.chunk;
+    for (int k = 0; k < nc; ++k) {
+        S.ctile[q][rc + k] = t;
+        const int a = base + k * S.chunk;
+        S.crange[q][rc + k] = make_int2(a, min(a + S.chunk, base + c));
+    }
+}
+
+// Tile scan of one simulation after a push into buffer set q (one block of 1024 threads):
+// per tile the particles now in set q (tcnt) and its frame count (fcnt) give
+//   set q:      tnum, the chunk offsets coff and the chunk map (ctile, crange) over the
+//               slots toff[q] set by the previous scan;
+//   set 1 - q:  toff = exclusive scan of tcnt + fcnt, the slots of the next step's push;
+// the particle total goes to n_next; the counts, cursors and frame counts are cleared.
+// `compact` (set-up): toff[q] = exclusive scan of tcnt first (no slack: the particles are
+// then placed there by the caller) and set 1 - q is left alone.
+__device__ void scan_counts(const SimDev& S, int q, bool compact)
 {
     __shared__ int s_warp[32];
     const int n = S.nptiles;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int per = (n + nth - 1) / nth;
     const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
-    int lp = 0, lc = 0;
+    int lp = 0, lc = 0, lk = 0;
     for (int i = i0; i < i1; ++i) {
         const int c = S.tcnt[i];
         lp += c;
         lc += (c + S.chunk - 1) / S.chunk;
+        lk += c + S.fcnt[i];
     }
     int rp = block_exclusive_scan(lp, s_warp);
     int rc = block_exclusive_scan(lc, s_warp);
-    int* to = S.toff[outpar];
-    int* co = S.coff[outpar];
-    int* ct = S.ctile[outpar];
+    int rk = block_exclusive_scan(lk, s_warp);
+    if (tid == nth - 1) atomicAdd(&S.st->n_next, rp + lp);
     for (int i = i0; i < i1; ++i) {
         const int c = S.tcnt[i];
-        const int nc = (c + S.chunk - 1) / S.chunk;
-        to[i] = rp;
-        co[i] = rc;
-        for (int k = 0; k < nc; ++k) ct[rc + k] = i;
+        if (compact) S.toff[q][i] = rp;
+        const int base = compact ? rp : S.toff[q][i];
+        S.tnum[q][i] = c;
+        S.coff[q][i] = rc;
+        write_chunks(S, q, i, base, c, rc);
+        if (!compact) S.toff[1 - q][i] = rk;
         rp += c;
-        rc += nc;
+        rc += (c + S.chunk - 1) / S.chunk;
+        rk += c + S.fcnt[i];
         S.tcnt[i] = 0;
         S.tcur[i] = 0;
+        S.fcnt[i] = 0;
     }
     if (tid == nth - 1) {
-        to[n] = rp;
-        co[n] = rc;
+        if (compact) S.toff[q][n] = rp;
+        else S.toff[1 - q][n] = rk;
+        S.coff[q][n] = rc;
     }
     __syncthreads();
 }
@@ -656,55 +781,122 @@ __device__ void scan_counts(const SimDev& S, int outpar)
 __global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims)
 {
     const SimDev& S = sims[blockIdx.x];
-    scan_counts(S, 1 - S.st->parity);
+    scan_counts(S, 1 - S.st->parity, false);
 }
 
-__global__ void __launch_bounds__(1024) k_scan_one(const SimDev* __restrict__ sim)
+// set-up: counts of the particles about to be placed into set q
+__global__ void __launch_bounds__(1024) k_scan_one(const SimDev* __restrict__ sim, int q)
 {
-    scan_counts(*sim, 1 - sim->st->parity);
+    scan_counts(*sim, q, true);
+}
+
+// set-up, after the particles sit in set q: frame counts of every particle ...
+template <int D>
+__global__ void k_frame_linear(const SimDev* __restrict__ sim, int q, long long n)
+{
+    const SimDev& S = *sim;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const unsigned cl = S.cell[q][p];
+        if (cl == DEAD) continue;
+        int c[3];
+        decode_cell<D>(S, cl, c);
+        int tc[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            tc[d] = c[d] / S.pt[d];
+            T[d] = tc[d] * S.pt[d];
+        }
+        // every neighbour tile whose one-cell frame holds c
+        constexpr int NF = D == 1 ? 3 : (D == 2 ? 9 : 27);
+        for (int k = 0; k < NF; ++k) {
+            int r = k, nt = 0, mul = 1;
+            bool ok = true, nz = false;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int f = r % 3 - 1;
+                r /= 3;
+                const int l = c[d] - T[d];
+                ok = ok && (f == 0 || (f < 0 ? l == 0 : l == S.pt[d] - 1));
+                const int tcd = tc[d] + f;
+                ok = ok && tcd >= 0 && tcd < S.npt[d];
+                nz = nz || f != 0;
+                nt += tcd * mul;
+                mul *= S.npt[d];
+            }
+            if (ok && nz) atomicAdd(&S.fcnt[nt], 1);
+        }
+    }
+}
+
+// ... then the slots of set 1 - q: exclusive scan of tnum[q] + fcnt (one block)
+__global__ void __launch_bounds__(1024) k_next_slots(const SimDev* __restrict__ sim, int q)
+{
+    const SimDev& S = *sim;
+    __shared__ int s_warp[32];
+    const int n = S.nptiles;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int per = (n + nth - 1) / nth;
+    const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
+    int lk = 0;
+    for (int i = i0; i < i1; ++i) lk += S.tnum[q][i] + S.fcnt[i];
+    int rk = block_exclusive_scan(lk, s_warp);
+    for (int i = i0; i < i1; ++i) {
+        S.toff[1 - q][i] = rk;
+        rk += S.tnum[q][i] + S.fcnt[i];
+        S.fcnt[i] = 0;
+    }
+    if (tid == nth - 1) S.toff[1 - q][n] = rk;
 }
 
 // Tile scan of one simulation over several blocks (decoupled look-back): block b (in the
 // order blocks start, from a ticket) scans tiles [4096 b, 4096 (b + 1)), publishes its
 // aggregate, then adds the totals of the blocks before it -- each published as
-// (status << 62) | (particles << 31) | chunks, status 1 aggregate, 2 inclusive prefix --
+// (status << 62) | (slots << 31) | chunks, status 1 aggregate, 2 inclusive prefix --
 // waiting (bounded) only on blocks that started earlier.  A wait that gives up flags a
 // timeout and takes prefix 0, which keeps every offset inside the particle arrays.
+// Outputs as scan_counts (not compact).
 __global__ void __launch_bounds__(1024) k_scan_lb(const SimDev* __restrict__ sims)
 {
     const SimDev& S = sims[0];
     __shared__ int s_warp[32];
     __shared__ int s_cnt[4096];
-    __shared__ int s_b, s_tp, s_tc, s_pp, s_pc;
+    __shared__ int s_tk, s_tc, s_pk, s_pc;
+    __shared__ int s_b;
     const int tid = threadIdx.x;
     if (tid == 0) s_b = atomicAdd(S.scanticket, 1);
     __syncthreads();
     const int b = s_b, n = S.nptiles, base = b * 4096;
-    const int outpar = 1 - S.st->parity;
+    const int q = 1 - S.st->parity;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int i = base + k * 1024 + tid;
         s_cnt[k * 1024 + tid] = i < n ? S.tcnt[i] : 0;
     }
     __syncthreads();
-    int c4[4], lp = 0, lc = 0;
+    int c4[4], f4[4], lp = 0, lc = 0, lk = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+        const int i = base + tid * 4 + k;
         c4[k] = s_cnt[tid * 4 + k];
+        f4[k] = i < n ? S.fcnt[i] : 0;
         lp += c4[k];
         lc += (c4[k] + S.chunk - 1) / S.chunk;
+        lk += c4[k] + f4[k];
     }
     int rp = block_exclusive_scan(lp, s_warp);
     int rc = block_exclusive_scan(lc, s_warp);
+    int rk = block_exclusive_scan(lk, s_warp);
     if (tid == 1023) {
-        s_tp = rp + lp;
+        s_tk = rk + lk;
         s_tc = rc + lc;
+        atomicAdd(&S.st->n_next, rp + lp);
     }
     __syncthreads();
     if (tid == 0) {
         unsigned long long* fl = S.scanflags;
-        const unsigned long long agg = ((unsigned long long)s_tp << 31) | (unsigned long long)s_tc;
-        long long pp = 0, pc = 0;
+        const unsigned long long agg = ((unsigned long long)s_tk << 31) | (unsigned long long)s_tc;
+        long long pk = 0, pc = 0;
         if (b == 0) {
             atomicExch(&fl[0], (2ull << 62) | agg);
         } else {
@@ -720,42 +912,40 @@ __global__ void __launch_bounds__(1024) k_scan_lb(const SimDev* __restrict__ sim
                     ok = false;
                     break;
                 }
-                pp += (long long)((f >> 31) & 0x7FFFFFFFull);
+                pk += (long long)((f >> 31) & 0x7FFFFFFFull);
                 pc += (long long)(f & 0x7FFFFFFFull);
                 if ((f >> 62) == 2) break;
             }
             if (!ok) {
                 atomicOr(&S.st->status, (unsigned)FLAG_TIMEOUT);
-                pp = pc = 0;
+                pk = pc = 0;
             }
-            atomicExch(&fl[b], (2ull << 62) | ((unsigned long long)(pp + s_tp) << 31) |
+            atomicExch(&fl[b], (2ull << 62) | ((unsigned long long)(pk + s_tk) << 31) |
                                    (unsigned long long)(pc + s_tc));
         }
-        s_pp = (int)pp;
+        s_pk = (int)pk;
         s_pc = (int)pc;
     }
     __syncthreads();
-    rp += s_pp;
+    rk += s_pk;
     rc += s_pc;
-    int* to = S.toff[outpar];
-    int* co = S.coff[outpar];
-    int* ct = S.ctile[outpar];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int i = base + tid * 4 + k;
         if (i >= n) break;
         const int c = c4[k];
-        const int nc = (c + S.chunk - 1) / S.chunk;
-        to[i] = rp;
-        co[i] = rc;
-        for (int q = 0; q < nc; ++q) ct[rc + q] = i;
-        rp += c;
-        rc += nc;
+        S.tnum[q][i] = c;
+        S.coff[q][i] = rc;
+        write_chunks(S, q, i, S.toff[q][i], c, rc);
+        S.toff[1 - q][i] = rk;
+        rc += (c + S.chunk - 1) / S.chunk;
+        rk += c + f4[k];
         S.tcnt[i] = 0;
         S.tcur[i] = 0;
+        S.fcnt[i] = 0;
         if (i == n - 1) {
-            to[n] = rp;
-            co[n] = rc;
+            S.toff[1 - q][n] = rk;
+            S.coff[q][n] = rc;
         }
     }
 }
@@ -799,18 +989,6 @@ __device__ __forceinline__ void copy_particle(const SimDev& S, int from, long lo
     S.pid[to][q] = S.pid[from][p];
 }
 
-// Reserve destination slots for a warp's particles (tile < 0: nothing to place).
-__device__ __forceinline__ int warp_reserve(int tile, int* cursors)
-{
-    const unsigned peers = __match_any_sync(0xffffffffu, tile);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    int base = 0;
-    if (tile >= 0 && lane == leader) base = atomicAdd(&cursors[tile], __popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return base + rank;
-}
 
 // Cell of c as an index of the tile-major cell arrays: tile * tvol + the cell's rank
 // within its tile, x fastest (the order the seeded slab is placed in).
@@ -837,12 +1015,11 @@ __device__ __forceinline__ int cell_key(const SimDev& S, const int c[3], int* ti
 
 constexpr int SCATTER_NP = 2;
 
-// Scatter of one chunk per work item: each warp reserves destination slots with one atomic
-// per distinct destination among its lanes (lanes going to the same destination write
-// consecutive slots).  The destination is the tile (slots after the tile's offset in the
-// order warps arrive) or, with SORT and a cell sort set up, the cell (slots after the
-// cell's offset within its tile, so that the tile comes out ordered by cell).
-template <int D, typename R, bool SORT>
+// Cell-sort scatter of one chunk per work item (simulations with a cell sort, pushed in
+// place this step): each warp reserves destination slots with one atomic per distinct cell
+// among its lanes (lanes of one cell write consecutive slots), after the cell's offset
+// within its tile, so that every tile of the other buffer set comes out ordered by cell.
+template <int D, typename R>
 __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims, int nsims,
                                                  const int* __restrict__ gprefix, int* __restrict__ counter)
 {
@@ -856,9 +1033,8 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
         if (item >= gprefix[nsims]) break;
         const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
         const SimDev& S = sims[ck.sim];
+        if (S.ccur == nullptr) continue;     // placed by the push
         const int par = S.st->parity, np = 1 - par;
-        const bool by_cell = SORT && S.ccur != nullptr;
-        int* cur = by_cell ? S.ccur : S.tcur;
         // SCATTER_NP particles per thread and round, all their loads issued before the slot
         // reservations (more loads in flight per thread)
         for (int base = ck.p0; base < ck.p1; base += SCATTER_NP * nth) {
@@ -884,14 +1060,9 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
                 if (cl[k] != DEAD) {
                     int c[3];
                     decode_cell<D>(S, cl[k], c);
-                    if (by_cell) {
-                        key = cell_key<D>(S, c, &t);
-                    } else {
-                        t = tile_of<D>(S, c);
-                        key = t;
-                    }
+                    key = cell_key<D>(S, c, &t);
                 }
-                const int slot = warp_reserve(key, cur);
+                const int slot = warp_reserve(key, S.ccur);
                 if (t >= 0) {
                     const long long q = (long long)S.toff[np][t] + slot;
                     S.cell[np][q] = cl[k];
@@ -996,7 +1167,8 @@ __global__ void __launch_bounds__(1024) k_step_end(const SimDev* __restrict__ si
         const SimDev& S = sims[i];
         DevState* st = S.st;
         const int np = 1 - st->parity;
-        st->n_alive = S.toff[np][S.nptiles];
+        st->n_alive = st->n_next;
+        st->n_next = 0;
         st->parity = np;
         st->step += 1;
         l += S.coff[np][S.nptiles];
@@ -1166,21 +1338,16 @@ __global__ void k_place_slab(const SimDev* __restrict__ sim, long long n, int pp
 
 // ---- host launch wrappers ------------------------------------------------------------
 template <int D, typename R>
-static void push_t(const Group& g, cudaStream_t s)
+static void push_t(const Group& g, bool sorting, cudaStream_t s)
 {
-    k_push<D, R><<<g.push_grid, 256, g.push_smem, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 0);
-}
-template <int D, typename R>
-static void scatter_t(const Group& g, cudaStream_t s)
-{
-    k_scatter<D, R, false><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
+    k_push<D, R><<<g.push_grid, 256, g.push_smem, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 0, sorting ? 1 : 0);
 }
 template <int D, typename R>
 static void cellsort_t(const Group& g, cudaStream_t s)
 {
     k_cellcount<D><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 3);
     k_cellscan<<<dim3((unsigned)g.cellscan_grid, (unsigned)g.nsims), 256, 0, s>>>(g.sims);
-    k_scatter<D, R, true><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
+    k_scatter<D, R><<<g.scatter_grid, 256, 0, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 1);
 }
 
 #define SFF_DISPATCH(dim, prec, FN, ...)                                 \
@@ -1196,9 +1363,8 @@ static void cellsort_t(const Group& g, cudaStream_t s)
         }                                                                \
     } while (0)
 
-void launch_push(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, push_t, g, s); }
-void launch_scatter(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, scatter_t, g, s); }
-void launch_scatter_sorted(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, cellsort_t, g, s); }
+void launch_push(const Group& g, bool sorting, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, push_t, g, sorting, s); }
+void launch_cell_sort(const Group& g, cudaStream_t s) { SFF_DISPATCH(g.dim, g.prec, cellsort_t, g, s); }
 void launch_scan(const Group& g, cudaStream_t s)
 {
     // a single simulation scans its tiles over several blocks; a batch, one block per member
@@ -1231,7 +1397,19 @@ void launch_incident_grid(const Group& g, cudaStream_t s)
         else incgrid_t<3, float>(g, s);
     }
 }
-void launch_scan_one(const SimDev* sim, int, int, cudaStream_t s) { k_scan_one<<<1, 1024, 0, s>>>(sim); }
+void launch_scan_one(const SimDev* sim, int q, cudaStream_t s) { k_scan_one<<<1, 1024, 0, s>>>(sim, q); }
+
+template <int D, typename R>
+static void frame_t(const SimDev* sim, int q, long long n, cudaStream_t s)
+{
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+    if (n > 0) k_frame_linear<D><<<grid, 256, 0, s>>>(sim, q, n);
+    k_next_slots<<<1, 1024, 0, s>>>(sim, q);
+}
+void launch_next_slots(const SimDev* sim, int dim, int prec, int q, long long n, cudaStream_t s)
+{
+    SFF_DISPATCH(dim, prec, frame_t, sim, q, n, s);
+}
 
 template <int D, typename R>
 static void gen_t(const SimDev* sim, long long n, int ppc, const int lo[3], const int sn[3], unsigned long long seed,
@@ -1296,7 +1474,7 @@ int prepare_push(int dim, int prec, size_t smem)
 template <int D, typename R>
 static void attr_scatter(int* out)
 {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_scatter<D, R, false>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_scatter<D, R>, 256, 0);
 }
 int scatter_blocks_per_sm(int dim, int prec)
 {

@@ -18,7 +18,7 @@ constexpr unsigned DEAD = 0xFFFFFFFFu;
 constexpr int EXIT_DOUBLES = 6;    // u[3], w, id, step
 
 enum Beam { BEAM_NONE = 0, BEAM_PLANE = 1, BEAM_LP = 2, BEAM_RP = 3, BEAM_UNIFORM = 4, BEAM_GAUSS2D = 5 };
-enum Flag { FLAG_TIMEOUT = 1u, FLAG_CFL = 2u, FLAG_EXIT_OVERFLOW = 4u };
+enum Flag { FLAG_TIMEOUT = 1u, FLAG_CFL = 2u, FLAG_EXIT_OVERFLOW = 4u, FLAG_CAPACITY = 8u };
 
 // Device-updated state of one simulation.
 struct DevState {
@@ -27,7 +27,9 @@ struct DevState {
     int n_alive;
     int n_exits;          // exit records claimed (may exceed capacity; then FLAG_EXIT_OVERFLOW)
     unsigned status;
-    long long pad[5];
+    int n_next;           // particles placed by the running step (summed by the tile scan)
+    int pad0;
+    long long pad[4];
 };
 
 // Incident-field constants in the working precision R, computed on the host at set-up.
@@ -89,19 +91,26 @@ struct alignas(128) SimDev {
     float frf[3];
     // device buffers
     void* F;                  // fields: [9][na_z][na_y][na_x], element (0,0,0) is a ghost corner
+    // Particle buffer sets: tile t of set q owns slots [toff[q][t], toff[q][t+1]) and holds
+    // its tnum[q][t] particles in the first of them; the slack after them bounds exactly
+    // the particles one step can bring in (those within one cell outside the tile).
     unsigned* cell[2];        // packed cell index per particle (DEAD = removed)
     void* off[2][3];          // in-cell offset in [0,1) per resolved axis
     void* mom[2][3];          // momentum gamma*v
     void* wgt[2];
     unsigned* pid[2];
-    int* toff[2];             // tile offsets [nptiles + 1] of each buffer set
+    int* toff[2];             // first slot of each tile [nptiles + 1] of each buffer set
+    int* tnum[2];             // particles of each tile [nptiles] of each buffer set
     int* coff[2];             // chunk offsets [nptiles + 1]: tile t owns chunks coff[t] .. coff[t+1]-1
     int* ctile[2];            // chunk -> tile map [max_chunks]
+    int2* crange[2];          // chunk -> particle slots [p0, p1) [max_chunks]
     int chunk;                // particles per chunk (the unit of work of push and scatter)
     int lane_p;               // push lane stride: particles per cell rounded down to 1, 2, 4 or 8
     int max_chunks;
     int* tcnt;                // per-tile counts of the next step
-    int* tcur;                // per-tile write cursors
+    int* tcur;                // per-tile write cursors of the push
+    int* fcnt;                // per-tile frame counts of the next step: particles within one
+                              // cell outside the tile (the most that can enter it in a step)
     int* ccnt;                // cell sort: per-cell counts [nptiles][tvol] (tile-major, x fastest
                               // within a tile), zero between sorts; NULL without cell sort
     int* ccur;                // cell sort: per-cell write cursors (offsets within the tile)
@@ -111,7 +120,7 @@ struct alignas(128) SimDev {
     int nscanblk;             // blocks of the multi-block tile scan (tiles / 4096, rounded up)
     double* exits;            // [max_exits][EXIT_DOUBLES]
     long long max_exits;
-    long long cap;            // particle capacity per buffer set
+    long long cap;            // slots per buffer set (frame factor x particle capacity)
     DevState* st;
     double* rho_ion;          // [na_z][na_y][na_x] ion charge density (diagnostics)
     double* scratch;          // diagnostics scratch: charge density, same layout

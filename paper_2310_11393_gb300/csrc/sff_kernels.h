@@ -50,12 +50,14 @@ __host__ __device__ constexpr size_t yee3_smem(int es)
 
 // per-step kernels (asynchronous)
 void launch_prefix(const Group& g, cudaStream_t s);
-void launch_push(const Group& g, cudaStream_t s);
+// push + deposit; each particle goes straight into its destination tile's slots of the
+// other buffer set (`sorting`: members with a cell sort are pushed in place instead and
+// placed by launch_cell_sort)
+void launch_push(const Group& g, bool sorting, cudaStream_t s);
 void launch_scan(const Group& g, cudaStream_t s);
-void launch_scatter(const Group& g, cudaStream_t s);
-// the re-sort of a cell-sort step: cell counts, per-tile cell scan, scatter by cell
-// (members without cell-sort arrays are scattered by tile)
-void launch_scatter_sorted(const Group& g, cudaStream_t s);
+// the placement of a cell-sort step: cell counts, per-tile cell scan, scatter by cell of
+// the members that have a cell sort (after launch_push(.., true, ..) and the tile scan)
+void launch_cell_sort(const Group& g, cudaStream_t s);
 void launch_yee(const Group& g, cudaStream_t s);
 void launch_step_end(const Group& g, cudaStream_t s);
 void launch_incident_grid(const Group& g, cudaStream_t s);
@@ -67,7 +69,10 @@ void launch_count_linear(const SimDev* sim, int dim, int prec, long long n, cuda
 void launch_sort_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s);
 void launch_place_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int lo[3], const int hi[3],
                        cudaStream_t s);
-void launch_scan_one(const SimDev* sim, int dim, int prec, cudaStream_t s);
+// set-up: compact slots of set q from the counts, then (after the particles are placed)
+// the frame counts of its n particles and the slots of set 1 - q
+void launch_scan_one(const SimDev* sim, int q, cudaStream_t s);
+void launch_next_slots(const SimDev* sim, int dim, int prec, int q, long long n, cudaStream_t s);
 
 // diagnostics
 void launch_charge(const SimDev* sim, int dim, int prec, long long n_alive, double* rho, cudaStream_t s);

@@ -62,6 +62,7 @@ struct pic_sim {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     long long nalloc_tot = 0;    // na_x*na_y*na_z
+    long long pcap = 0;          // particle capacity (the buffer sets hold h.cap slots)
 };
 
 

@@ -22,7 +22,7 @@ PIC_BEAM_NONE, PIC_BEAM_PLANE, PIC_BEAM_LP, PIC_BEAM_RP, PIC_BEAM_UNIFORM = 0, 1
 PIC_ENV_SIN2, PIC_ENV_GAUSS = 0, 1
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_DIAG_ENERGIES, PIC_DIAG_GAUSS, PIC_DIAG_PARTICLES, PIC_DIAG_EXITS, PIC_DIAG_FIELDS = 0, 1, 2, 3, 4
-PIC_FLAG_TIMEOUT, PIC_FLAG_CFL, PIC_FLAG_EXIT_OVERFLOW = 1, 2, 4
+PIC_FLAG_TIMEOUT, PIC_FLAG_CFL, PIC_FLAG_EXIT_OVERFLOW, PIC_FLAG_CAPACITY = 1, 2, 4, 8
 
 
 class pic_config(Structure):

@@ -63,12 +63,13 @@ def test_counts_and_footprint(P):
     w = synth.c2_2d_lp()
     p = P.pic_derive_params(P.config_from(w))
     assert p.n_particles == 2097152
-    # fields (2 sets of E,B + 2 J) + 2 particle buffer sets + diagnostics, well under 1 GB
+    # fields (2 sets of E,B + 2 J) + 2 particle buffer sets of 2^dim slots per particle
+    # (the tiles' slack for arrivals) + diagnostics
     assert 0.1e9 < p.device_bytes < 1e9
     w3 = synth.c3_3d_rp()
     p3 = P.pic_derive_params(P.config_from(w3))
     assert p3.n_particles == 16777216
-    assert p3.device_bytes < 10e9
+    assert p3.device_bytes < 16e9
 
 
 @pytest.mark.parametrize("bad,frag", [
