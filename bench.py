@@ -64,7 +64,7 @@ INCIDENT_GRID = 0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from the
 # ncu capture summarised in profiles/ (kept in step with the kernel: set to None when the
 # kernel changes and until it is captured again)
-PROFILED_TRAFFIC = {("2d_lp_1024sq", "k_push<2,float>"): (78.4e6, "profiles/k_push_2d_lp_1024sq.md, past the focus")}
+PROFILED_TRAFFIC = {("2d_lp_1024sq", "k_push<2,float>"): (116.4e6, "profiles/k_push_2d_lp_1024sq.md, step 760 (focus)")}
 
 
 def workload(name):
@@ -156,11 +156,12 @@ def flops_per_push(w):
 
 
 def bytes_per_push(w):
-    """Algorithmic HBM bytes of one push: particle state read (cell, offsets, momenta, weight)
-    and written (cell, offsets, momenta), plus the field and current grid traffic shared by
-    the ppc particles of a cell (E, B read once; J read-modify-write once)."""
+    """Algorithmic HBM bytes of one push: the particle record (cell, offsets, momenta, weight,
+    id) read from one buffer set and written into its destination tile of the other, plus
+    the field and current grid traffic shared by the ppc particles of a cell (E, B read
+    once; J read-modify-write once)."""
     es = 4 if w.precision == synth.FP32 else 8
-    part = (4 + w.dim * es + 3 * es + es) + (4 + w.dim * es + 3 * es)
+    part = 2 * (4 + w.dim * es + 3 * es + es + 4)
     grid = (6 * es + 2 * 3 * es) / max(w.ppc, 1)
     return part + grid
 
@@ -279,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
             "yee": {"ms": round(yee_s * 1e3, 4), "achieved_gbs": round(yee_bytes / yee_s / 1e9, 1),
                     "frac_of_hbm": round(yee_bytes / yee_s / 1e9 / hbm, 4), "bytes_per_cell": 18 * es},
             "phases_ms": [round(x / nsteps_prof * 1e3, 4) for x in prof],
-            "phases": ["push+deposit", "tile scan", "scatter", "field solve", "step end"],
+            "phases": ["push+deposit+placement", "tile scan", "cell-sort placement", "field solve", "step end"],
             "windows": windows}
 
     e2e = None
