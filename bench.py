@@ -202,7 +202,7 @@ def run_ours(args, rank, world, local_rank):
     tune = {"trial_steps": args.autotune}
     if args.autotune > 0:
         t0 = time.perf_counter()
-        tune["ms_per_step_at_focus"] = round(pic.pic_autotune(cfg, args.autotune, stream), 4)
+        tune["ms_per_step_trial"] = round(pic.pic_autotune(cfg, args.autotune, stream), 4)
         tune["seconds"] = round(time.perf_counter() - t0, 2)
     prm = pic.pic_derive_params(cfg)
     tune["push_tile"] = list(prm.tile)[: w.dim]

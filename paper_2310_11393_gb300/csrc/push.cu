@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
     }
     __syncthreads();
     unsigned phase = 0;
+    int acq_sim = -1;         // thread 0: the simulation whose tensor maps it has acquired
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -297,8 +298,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         // box: x nodes [T0-4, T0+pt+4), y/z nodes [T0-2, T0+pt+3); array index = node + G
         const int org[3] = {T0[0] - 4 + G, D > 1 ? T0[1] - 2 + G : 0, D > 2 ? T0[2] - 2 + G : 0};
         if (tid == 0) {
-            tensormap_acquire(&S.tm_pf);
-            tensormap_acquire(&S.tm_pj);
+            // the maps were written to device memory before the launch: one acquire per
+            // simulation and block orders that write before this thread's TMA uses
+            if (ck.sim != acq_sim) {
+                tensormap_acquire(&S.tm_pf);
+                tensormap_acquire(&S.tm_pj);
+                acq_sim = ck.sim;
+            }
             mbar_arrive_expect_tx(&bar, (unsigned)(6 * bvol * sizeof(R)));
             tma_load_box<D>(Fs, &S.tm_pf, org, S.incgrid ? COMP_TOTAL : comp_eb(par), &bar);
             // double-precision phase reference of this tile, once per tile

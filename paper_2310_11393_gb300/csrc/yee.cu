@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
         }
         if constexpr (D > 2) lo[2] = t * TZ;
     };
+    int acq_sim = -1;         // thread 0: the simulation whose tensor maps it has acquired
     auto issue = [&](int it, int b) {
         if (tid != 0) return;
         const Work w = work[it];
@@ -99,9 +100,13 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
         tile_lo(S, w.tile, l);
         const int o[3] = {l[0] - HX + G, D > 1 ? l[1] - HY + G : 0, D > 2 ? l[2] - HZ + G : 0};
         const int p = S.st->parity;
-        tensormap_acquire(&S.tm_yin);
-        tensormap_acquire(&S.tm_yj);
-        tensormap_acquire(&S.tm_yout);
+        // one acquire per simulation and block (the maps were written before the launch)
+        if (w.sim != acq_sim) {
+            tensormap_acquire(&S.tm_yin);
+            tensormap_acquire(&S.tm_yj);
+            tensormap_acquire(&S.tm_yout);
+            acq_sim = w.sim;
+        }
         unsigned char* box = smem_raw + b * BOXB;
         mbar_arrive_expect_tx(&bars[b], (unsigned)(9 * BV * sizeof(R)));
         tma_load_box<D>(box, &S.tm_yin, o, comp_eb(p), &bars[b]);
