@@ -191,7 +191,7 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
 
 /* Autotuner of the particle tile and the push work-item size (no counterpart in the paper:
  * a layout choice of this implementation).  For each candidate (tiles of 8..32 cells per
- * axis by dimension, then work items of 1024..4096 particles at the best tile) it creates
+ * axis by dimension, then work items of 256..4096 particles at the best tile) it creates
  * the simulation on the current device and times two stretches, each trial_steps untimed
  * steps and then the faster of two runs of trial_steps timed steps (CUDA events on
  * `stream`): one from t = 0, one with its clock moved to the time the pulse is on the

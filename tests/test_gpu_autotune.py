@@ -35,7 +35,7 @@ def test_every_candidate_tile_matches_the_oracle(P, orc, dim):
     ref.step(steps)
     pr, fr = ref.particles(), ref.fields()
     for tile in TILES[dim]:
-        for chunk in (1024, 4096):
+        for chunk in (256, 1024, 4096):
             sim = P.Simulation(P.config_from(w, tile=tile, chunk=chunk))
             assert list(sim.info().params.tile)[:dim] == list(tile)
             sim.step(steps)
@@ -54,7 +54,7 @@ def test_autotune_picks_a_candidate_and_caches_it(P):
     t1 = time.perf_counter()
     assert ms > 0
     assert tuple(c.tile)[:2] in TILES[2]
-    assert c.chunk in (1024, 2048, 4096)
+    assert c.chunk in (256, 512, 1024, 2048, 4096)
     c2 = P.config_from(w)
     ms2 = P.pic_autotune(c2, 3)
     t2 = time.perf_counter()
@@ -66,7 +66,7 @@ def test_init_with_autotune_runs_the_tuned_layout(P, orc):
     w = small_2d()
     sim = P.Simulation(P.config_from(w, autotune_steps=2))
     prm = sim.info().params
-    assert tuple(prm.tile)[:2] in TILES[2] and prm.chunk in (1024, 2048, 4096)
+    assert tuple(prm.tile)[:2] in TILES[2] and prm.chunk in (256, 512, 1024, 2048, 4096)
     sim.step(10)
     ref = orc.Sim(orc.config_from(w))
     ref.step(10)
