@@ -2,14 +2,18 @@
 //   k_push     gather + incident field + Boris + move + Esirkepov deposit, one particle tile
 //              per work item: the tile's field box arrives by one TMA load, the current is
 //              accumulated in shared memory and leaves by one TMA reduce-add (FP32) or one
-//              atomic per nonzero cell (FP64); destination-tile counts are histogrammed in
-//              shared memory first (one global atomic per neighbour tile);
-//   k_scan     per-simulation exclusive scan of the destination-tile counts;
-//   k_scatter  compaction by tile into the other buffer set with warp-aggregated slot
-//              reservation; every few steps, after k_cellcount / k_cellscan, by cell
-//              within the tile (the cell sort);
-//   k_step_end step counter and buffer parity.
-// Set-up kernels generate the seeded slab and sort arbitrary particle sets by tile.
+//              atomic per nonzero cell (FP64); every particle is written into its
+//              destination tile's slots of the other buffer set (warp-aggregated slot
+//              reservation); destination-tile and frame counts are histogrammed in shared
+//              memory first (one global atomic per neighbour tile);
+//   k_scan_lb / k_scan   tile scan: counts and work items of the set just written, slots
+//              of the other set for the next push (counts + frame counts);
+//   k_cellcount, k_cellscan, k_scatter   the opt-in cell sort: on its steps the push
+//              writes in place and these place each tile's particles in cell order;
+//   k_step_end step counter, particle count and buffer parity, and the next step's work
+//              item numbering (k_prefix does the latter alone when needed).
+// Set-up kernels generate the seeded slab, sort arbitrary particle sets by tile and set the
+// first slots.
 #include <cuda_runtime.h>
 
 #include <algorithm>
