@@ -110,3 +110,38 @@ def test_server_results_equal_alone(P, fill):
         assert r.submit_time <= r.start_time <= r.finish_time
         for j in (0, 2):
             assert abs(r.energies[j] - ea[j]) <= 1e-4 * abs(ea[j]), (k, j, r.energies[j], ea[j])
+
+
+def test_alone_batch_and_profiled_steps_interleave(P):
+    """One simulation advanced alone, in two different batches, one kernel at a time and
+    after a particle reload, in turns: each kind of step numbers its work items for its own
+    launch group, and a step after another group's (or after a new particle layout) first
+    renumbers them.  The result equals the same number of plain steps."""
+    ws = mix()
+    ref = P.Simulation(P.config_from(ws[0]))
+    ref.step(40)
+    pr, fr = ref.particles(), ref.fields()
+    ref.close()
+    a = P.Simulation(P.config_from(ws[0]))
+    b = P.Simulation(P.config_from(ws[1]))
+    c = P.Simulation(P.config_from(ws[2]))
+    a.step(5)
+    P.pic_batch_step([a.h, b.h], 5)
+    a.step(3)
+    P.pic_batch_step([c.h, a.h], 4)
+    P.pic_batch_step([a.h, b.h], 3)
+    P.pic_profile_step(a.h, 4)
+    a.step(2)
+    # a reload of the particles as they are (a new layout, same state)
+    p = a.particles()
+    a.set_particles(p["x"], p["u"], p["w"], p["id"])
+    P.pic_batch_step([a.h, b.h], 6)
+    a.step(8)
+    assert a.info().step == 40
+    pa = a.particles()
+    assert set(pa["id"].tolist()) == set(pr["id"].tolist())
+    err, n = momentum_error(pa, pr, ws[0].a0)
+    assert err < 1e-5, err
+    assert field_errors(a.fields(), fr)[:6].max() < 1e-5
+    for s in (a, b, c):
+        s.close()
