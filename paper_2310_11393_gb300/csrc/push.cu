@@ -150,8 +150,7 @@ __device__ __forceinline__ void boris_update(R u[3], const R E[3], const R B[3],
     R um[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
-    const R gm = m_sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-    const R tf = h / gm;
+    const R tf = h * m_rsqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);   // h / gamma^-
     const R tv[3] = {tf * B[0], tf * B[1], tf * B[2]};
     const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
     const R sf = R(2) / (R(1) + t2);
@@ -409,7 +408,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
             if (S.pusher == 1) vay_update<R>(u, E, B, hq);
             else if (S.pusher == 2) higuera_cary_update<R>(u, E, B, hq);
             else boris_update<R>(u, E, B, hq);
-            const R ig = R(1) / m_sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            const R ig = m_rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);   // 1 / gamma
             const R v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
 
             // ---- Esirkepov deposition of the move ----
