@@ -358,266 +358,266 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
             int tdst = -1;
             R on[3] = {R(0), R(0), R(0)}, u[3] = {R(0), R(0), R(0)}, wt = R(0);
             if (p < p1) {
-            const unsigned cl = S.cell[par][p];
-            int c[3];
-            decode_cell<D>(S, cl, c);
-            R o[3] = {R(0), R(0), R(0)};
+                const unsigned cl = S.cell[par][p];
+                int c[3];
+                decode_cell<D>(S, cl, c);
+                R o[3] = {R(0), R(0), R(0)};
 #pragma unroll
-            for (int d = 0; d < D; ++d) o[d] = reinterpret_cast<const R*>(S.off[par][d])[p];
+                for (int d = 0; d < D; ++d) o[d] = reinterpret_cast<const R*>(S.off[par][d])[p];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) u[d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
-            wt = reinterpret_cast<const R*>(S.wgt[par])[p];
+                for (int d = 0; d < 3; ++d) u[d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
+                wt = reinterpret_cast<const R*>(S.wgt[par])[p];
 
-            // ---- gather of the scattered field (order-2 shapes on the Yee stagger) ----
-            R Wp[3][3], Wd[3][3];
-            int lp[3] = {0, 0, 0}, ld[3] = {0, 0, 0};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (d < D) {
-                    const int h = o[d] >= R(0.5);
-                    shape2(o[d] - R(h), Wp[d]);
-                    lp[d] = c[d] + h - 1 - T0[d] + hx[d];
-                    shape2(o[d] - R(0.5), Wd[d]);
-                    ld[d] = c[d] - 1 - T0[d] + hx[d];
-                } else {
-                    Wp[d][0] = Wd[d][0] = R(1);
-                    Wp[d][1] = Wd[d][1] = Wp[d][2] = Wd[d][2] = R(0);
-                }
-            }
-            R E[3], B[3];
-            E[0] = interp<D, R>(Fs + 0 * bvol, bx, bxy, ld[0], lp[1], lp[2], Wd[0], Wp[1], Wp[2]);
-            E[1] = interp<D, R>(Fs + 1 * bvol, bx, bxy, lp[0], ld[1], lp[2], Wp[0], Wd[1], Wp[2]);
-            E[2] = interp<D, R>(Fs + 2 * bvol, bx, bxy, lp[0], lp[1], ld[2], Wp[0], Wp[1], Wd[2]);
-            B[0] = interp<D, R>(Fs + 3 * bvol, bx, bxy, lp[0], ld[1], ld[2], Wp[0], Wd[1], Wd[2]);
-            B[1] = interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
-            B[2] = interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
-
-            // ---- incident field at (x^n, t^n) (in a total-field run, or when it was
-            // evaluated on the grid, it is in the gathered field already) ----
-            if (!S.tf && !S.incgrid) {
-                R Ei[3], Bi[3];
-                incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
+                // ---- gather of the scattered field (order-2 shapes on the Yee stagger) ----
+                R Wp[3][3], Wd[3][3];
+                int lp[3] = {0, 0, 0}, ld[3] = {0, 0, 0};
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    E[d] += Ei[d];
-                    B[d] += Bi[d];
+                    if (d < D) {
+                        const int h = o[d] >= R(0.5);
+                        shape2(o[d] - R(h), Wp[d]);
+                        lp[d] = c[d] + h - 1 - T0[d] + hx[d];
+                        shape2(o[d] - R(0.5), Wd[d]);
+                        ld[d] = c[d] - 1 - T0[d] + hx[d];
+                    } else {
+                        Wp[d][0] = Wd[d][0] = R(1);
+                        Wp[d][1] = Wd[d][1] = Wp[d][2] = Wd[d][2] = R(0);
+                    }
                 }
-            }
+                R E[3], B[3];
+                E[0] = interp<D, R>(Fs + 0 * bvol, bx, bxy, ld[0], lp[1], lp[2], Wd[0], Wp[1], Wp[2]);
+                E[1] = interp<D, R>(Fs + 1 * bvol, bx, bxy, lp[0], ld[1], lp[2], Wp[0], Wd[1], Wp[2]);
+                E[2] = interp<D, R>(Fs + 2 * bvol, bx, bxy, lp[0], lp[1], ld[2], Wp[0], Wp[1], Wd[2]);
+                B[0] = interp<D, R>(Fs + 3 * bvol, bx, bxy, lp[0], ld[1], ld[2], Wp[0], Wd[1], Wd[2]);
+                B[1] = interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
+                B[2] = interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
 
-            // ---- momentum update, charge -1, mass 1 (u^{n-1/2} -> u^{n+1/2}) ----
-            if (S.pusher == 1) vay_update<R>(u, E, B, hq);
-            else if (S.pusher == 2) higuera_cary_update<R>(u, E, B, hq);
-            else boris_update<R>(u, E, B, hq);
-            const R ig = m_rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);   // 1 / gamma
-            const R v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
+                // ---- incident field at (x^n, t^n) (in a total-field run, or when it was
+                // evaluated on the grid, it is in the gathered field already) ----
+                if (!S.tf && !S.incgrid) {
+                    R Ei[3], Bi[3];
+                    incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        E[d] += Ei[d];
+                        B[d] += Bi[d];
+                    }
+                }
 
-            // ---- Esirkepov deposition of the move ----
-            // Per axis the old shape covers the old nearest node and its two neighbours; the
-            // new shape is shifted by sh in {-1, 0, 1} nodes (|move| < 1 cell), so both fit a
-            // window of four nodes starting one below the old support when sh = -1 and at it
-            // otherwise.  S0 / DS: old shape / shape change on that window.  Along the
-            // current's own axis the window's last partial sum is the total charge change,
-            // zero: one node fewer carries that component.  When no lane of the warp changes
-            // its nearest node along an axis (sh = 0 everywhere: most steps of most
-            // electrons), the window's fourth node is zero for every lane and the loops stop
-            // at three nodes on that axis (a warp-uniform bound).
-            R S0[3][4], DS[3][4];
-            int jw[3] = {0, 0, 0};
-            R mv[3] = {R(0), R(0), R(0)};
-            bool cross[3] = {false, false, false};
+                // ---- momentum update, charge -1, mass 1 (u^{n-1/2} -> u^{n+1/2}) ----
+                if (S.pusher == 1) vay_update<R>(u, E, B, hq);
+                else if (S.pusher == 2) higuera_cary_update<R>(u, E, B, hq);
+                else boris_update<R>(u, E, B, hq);
+                const R ig = m_rsqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);   // 1 / gamma
+                const R v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
+
+                // ---- Esirkepov deposition of the move ----
+                // Per axis the old shape covers the old nearest node and its two neighbours; the
+                // new shape is shifted by sh in {-1, 0, 1} nodes (|move| < 1 cell), so both fit a
+                // window of four nodes starting one below the old support when sh = -1 and at it
+                // otherwise.  S0 / DS: old shape / shape change on that window.  Along the
+                // current's own axis the window's last partial sum is the total charge change,
+                // zero: one node fewer carries that component.  When no lane of the warp changes
+                // its nearest node along an axis (sh = 0 everywhere: most steps of most
+                // electrons), the window's fourth node is zero for every lane and the loops stop
+                // at three nodes on that axis (a warp-uniform bound).
+                R S0[3][4], DS[3][4];
+                int jw[3] = {0, 0, 0};
+                R mv[3] = {R(0), R(0), R(0)};
+                bool cross[3] = {false, false, false};
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                mv[d] = dtdx * v[d];
-                const int h0 = o[d] >= R(0.5);
-                const R d0 = o[d] - R(h0);
-                const R r1 = d0 + mv[d];
-                const int sh = (int)m_floor(r1 + R(0.5));
-                const R d1 = r1 - R(sh);
-                R w0[3], w1[3];
-                shape2(d0, w0);
-                shape2(d1, w1);
-                const bool lo = sh < 0, hi = sh > 0;
-                cross[d] = sh != 0;
-                const R o0[4] = {lo ? R(0) : w0[0], lo ? w0[0] : w0[1], lo ? w0[1] : w0[2], lo ? w0[2] : R(0)};
-                const R n1[4] = {hi ? R(0) : w1[0], hi ? w1[0] : w1[1], hi ? w1[1] : w1[2], hi ? w1[2] : R(0)};
+                for (int d = 0; d < D; ++d) {
+                    mv[d] = dtdx * v[d];
+                    const int h0 = o[d] >= R(0.5);
+                    const R d0 = o[d] - R(h0);
+                    const R r1 = d0 + mv[d];
+                    const int sh = (int)m_floor(r1 + R(0.5));
+                    const R d1 = r1 - R(sh);
+                    R w0[3], w1[3];
+                    shape2(d0, w0);
+                    shape2(d1, w1);
+                    const bool lo = sh < 0, hi = sh > 0;
+                    cross[d] = sh != 0;
+                    const R o0[4] = {lo ? R(0) : w0[0], lo ? w0[0] : w0[1], lo ? w0[1] : w0[2], lo ? w0[2] : R(0)};
+                    const R n1[4] = {hi ? R(0) : w1[0], hi ? w1[0] : w1[1], hi ? w1[1] : w1[2], hi ? w1[2] : R(0)};
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    S0[d][m] = o0[m];
-                    DS[d][m] = n1[m] - o0[m];
+                    for (int m = 0; m < 4; ++m) {
+                        S0[d][m] = o0[m];
+                        DS[d][m] = n1[m] - o0[m];
+                    }
+                    jw[d] = c[d] + h0 - (lo ? 2 : 1) - T0[d] + hx[d];
                 }
-                jw[d] = c[d] + h0 - (lo ? 2 : 1) - T0[d] + hx[d];
-            }
-            // window width per axis over the lanes running here (each lane's own vote is in
-            // its mask, so its width covers its own window whatever the warp's convergence)
-            const unsigned am = __activemask();
-            int nw[3] = {4, 4, 4};
+                // window width per axis over the lanes running here (each lane's own vote is in
+                // its mask, so its width covers its own window whatever the warp's convergence)
+                const unsigned am = __activemask();
+                int nw[3] = {4, 4, 4};
 #pragma unroll
-            for (int d = 0; d < D; ++d) nw[d] = __any_sync(am, cross[d]) ? 4 : 3;
-            R* Jx = Js;
-            R* Jy = Js + bvol;
-            R* Jz = Js + 2 * bvol;
-            const R cw = jfac * wt;
-            const R third = R(1) / R(3);
-            if constexpr (D == 1) {
-                R acc = R(0);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (a >= nw[0] - 1) break;
-                    acc += cw * DS[0][a];
-                    sm_add(&Jx[jw[0] + a], acc);
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    if (a >= nw[0]) break;
-                    const R f = S0[0][a] + R(0.5) * DS[0][a];
-                    sm_add(&Jy[jw[0] + a], -wt * v[1] * f);
-                    sm_add(&Jz[jw[0] + a], -wt * v[2] * f);
-                }
-            } else if constexpr (D == 2) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    if (b >= nw[1]) break;
-                    const R fy = S0[1][b] + R(0.5) * DS[1][b];
+                for (int d = 0; d < D; ++d) nw[d] = __any_sync(am, cross[d]) ? 4 : 3;
+                R* Jx = Js;
+                R* Jy = Js + bvol;
+                R* Jz = Js + 2 * bvol;
+                const R cw = jfac * wt;
+                const R third = R(1) / R(3);
+                if constexpr (D == 1) {
                     R acc = R(0);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         if (a >= nw[0] - 1) break;
-                        acc += cw * DS[0][a] * fy;
-                        sm_add(&Jx[(jw[1] + b) * bx + jw[0] + a], acc);
+                        acc += cw * DS[0][a];
+                        sm_add(&Jx[jw[0] + a], acc);
                     }
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    if (a >= nw[0]) break;
-                    const R fx = S0[0][a] + R(0.5) * DS[0][a];
-                    R acc = R(0);
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        if (b >= nw[1] - 1) break;
-                        acc += cw * DS[1][b] * fx;
-                        sm_add(&Jy[(jw[1] + b) * bx + jw[0] + a], acc);
-                    }
-                }
-                const R qv = -wt * v[2];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    if (b >= nw[1]) break;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         if (a >= nw[0]) break;
-                        const R wz = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
-                                     R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
-                        sm_add(&Jz[(jw[1] + b) * bx + jw[0] + a], qv * wz);
+                        const R f = S0[0][a] + R(0.5) * DS[0][a];
+                        sm_add(&Jy[jw[0] + a], -wt * v[1] * f);
+                        sm_add(&Jz[jw[0] + a], -wt * v[2] * f);
                     }
-                }
-            } else {
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    if (cc >= nw[2]) break;
+                } else if constexpr (D == 2) {
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         if (b >= nw[1]) break;
-                        const R fyz = S0[1][b] * S0[2][cc] + R(0.5) * DS[1][b] * S0[2][cc] +
-                                      R(0.5) * S0[1][b] * DS[2][cc] + third * DS[1][b] * DS[2][cc];
+                        const R fy = S0[1][b] + R(0.5) * DS[1][b];
                         R acc = R(0);
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             if (a >= nw[0] - 1) break;
-                            acc += cw * DS[0][a] * fyz;
-                            sm_add(&Jx[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                            acc += cw * DS[0][a] * fy;
+                            sm_add(&Jx[(jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
-                }
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    if (cc >= nw[2]) break;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         if (a >= nw[0]) break;
-                        const R fxz = S0[0][a] * S0[2][cc] + R(0.5) * DS[0][a] * S0[2][cc] +
-                                      R(0.5) * S0[0][a] * DS[2][cc] + third * DS[0][a] * DS[2][cc];
+                        const R fx = S0[0][a] + R(0.5) * DS[0][a];
                         R acc = R(0);
 #pragma unroll
                         for (int b = 0; b < 3; ++b) {
                             if (b >= nw[1] - 1) break;
-                            acc += cw * DS[1][b] * fxz;
-                            sm_add(&Jy[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                            acc += cw * DS[1][b] * fx;
+                            sm_add(&Jy[(jw[1] + b) * bx + jw[0] + a], acc);
                         }
                     }
-                }
+                    const R qv = -wt * v[2];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    if (b >= nw[1]) break;
+                    for (int b = 0; b < 4; ++b) {
+                        if (b >= nw[1]) break;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        if (a >= nw[0]) break;
-                        const R fxy = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
-                                      R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
-                        R acc = R(0);
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            if (cc >= nw[2] - 1) break;
-                            acc += cw * DS[2][cc] * fxy;
-                            sm_add(&Jz[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                        for (int a = 0; a < 4; ++a) {
+                            if (a >= nw[0]) break;
+                            const R wz = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
+                                         R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
+                            sm_add(&Jz[(jw[1] + b) * bx + jw[0] + a], qv * wz);
                         }
                     }
-                }
-            }
-
-            // ---- move: carry the offset into the cell index; removal near the faces ----
-            int cn[3] = {c[0], c[1], c[2]};
-            bool dead = false;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const R x = o[d] + mv[d];
-                const R fl = m_floor(x);
-                R r = x - fl;
-                int k = (int)fl;
-                if (r >= R(1)) {
-                    r -= R(1);
-                    k += 1;
-                }
-                cn[d] = c[d] + k;
-                on[d] = r;
-                if (cn[d] < S.margin || cn[d] >= S.n[d] - S.margin) dead = true;
-            }
-            if (dead) {
-                const int slot = atomicAdd(&st->n_exits, 1);
-                if (slot < S.max_exits) {
-                    double* e = S.exits + (long long)slot * EXIT_DOUBLES;
-                    e[0] = (double)u[0];
-                    e[1] = (double)u[1];
-                    e[2] = (double)u[2];
-                    e[3] = (double)wt;
-                    e[4] = (double)S.pid[par][p];
-                    e[5] = (double)st->step;
                 } else {
-                    atomicOr(&st->status, (unsigned)FLAG_EXIT_OVERFLOW);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        if (cc >= nw[2]) break;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            if (b >= nw[1]) break;
+                            const R fyz = S0[1][b] * S0[2][cc] + R(0.5) * DS[1][b] * S0[2][cc] +
+                                          R(0.5) * S0[1][b] * DS[2][cc] + third * DS[1][b] * DS[2][cc];
+                            R acc = R(0);
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                if (a >= nw[0] - 1) break;
+                                acc += cw * DS[0][a] * fyz;
+                                sm_add(&Jx[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        if (cc >= nw[2]) break;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            if (a >= nw[0]) break;
+                            const R fxz = S0[0][a] * S0[2][cc] + R(0.5) * DS[0][a] * S0[2][cc] +
+                                          R(0.5) * S0[0][a] * DS[2][cc] + third * DS[0][a] * DS[2][cc];
+                            R acc = R(0);
+#pragma unroll
+                            for (int b = 0; b < 3; ++b) {
+                                if (b >= nw[1] - 1) break;
+                                acc += cw * DS[1][b] * fxz;
+                                sm_add(&Jy[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if (b >= nw[1]) break;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            if (a >= nw[0]) break;
+                            const R fxy = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
+                                          R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
+                            R acc = R(0);
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) {
+                                if (cc >= nw[2] - 1) break;
+                                acc += cw * DS[2][cc] * fxy;
+                                sm_add(&Jz[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                            }
+                        }
+                    }
                 }
-            } else {
-                // destination tile relative to this one (a move is under one cell per axis)
-                int hidx = 0, mul = 1, tg = 0, tmul = 1;
-                int rel[3] = {0, 0, 0};
+
+                // ---- move: carry the offset into the cell index; removal near the faces ----
+                int cn[3] = {c[0], c[1], c[2]};
+                bool dead = false;
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    rel[d] = cn[d] < T0[d] ? -1 : (cn[d] >= T0[d] + S.pt[d] ? 1 : 0);
-                    hidx += (rel[d] + 1) * mul;
-                    mul *= 3;
-                    tg += (tc[d] + rel[d]) * tmul;
-                    tmul *= S.npt[d];
+                    const R x = o[d] + mv[d];
+                    const R fl = m_floor(x);
+                    R r = x - fl;
+                    int k = (int)fl;
+                    if (r >= R(1)) {
+                        r -= R(1);
+                        k += 1;
+                    }
+                    cn[d] = c[d] + k;
+                    on[d] = r;
+                    if (cn[d] < S.margin || cn[d] >= S.n[d] - S.margin) dead = true;
                 }
-                atomicAdd(&s_hist[hidx], 1);
-                frame_count<D>(S, cn, T0, rel, s_frame);
-                ncl = encode_cell<D>(S, cn);
-                tdst = tg;
-            }
-            if (!direct) {
-                S.cell[par][p] = ncl;
+                if (dead) {
+                    const int slot = atomicAdd(&st->n_exits, 1);
+                    if (slot < S.max_exits) {
+                        double* e = S.exits + (long long)slot * EXIT_DOUBLES;
+                        e[0] = (double)u[0];
+                        e[1] = (double)u[1];
+                        e[2] = (double)u[2];
+                        e[3] = (double)wt;
+                        e[4] = (double)S.pid[par][p];
+                        e[5] = (double)st->step;
+                    } else {
+                        atomicOr(&st->status, (unsigned)FLAG_EXIT_OVERFLOW);
+                    }
+                } else {
+                    // destination tile relative to this one (a move is under one cell per axis)
+                    int hidx = 0, mul = 1, tg = 0, tmul = 1;
+                    int rel[3] = {0, 0, 0};
 #pragma unroll
-                for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
+                    for (int d = 0; d < D; ++d) {
+                        rel[d] = cn[d] < T0[d] ? -1 : (cn[d] >= T0[d] + S.pt[d] ? 1 : 0);
+                        hidx += (rel[d] + 1) * mul;
+                        mul *= 3;
+                        tg += (tc[d] + rel[d]) * tmul;
+                        tmul *= S.npt[d];
+                    }
+                    atomicAdd(&s_hist[hidx], 1);
+                    frame_count<D>(S, cn, T0, rel, s_frame);
+                    ncl = encode_cell<D>(S, cn);
+                    tdst = tg;
+                }
+                if (!direct) {
+                    S.cell[par][p] = ncl;
 #pragma unroll
-                for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
-            }
+                    for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
+                }
             }
             // ---- placement into the destination tile's slots of the other buffer set (all
             // lanes of the warp take part in the reservation) ----
