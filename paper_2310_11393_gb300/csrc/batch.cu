@@ -1,6 +1,7 @@
 // Batched stepping of independent simulations (pic_batch_step): simulations of the
 // same dimension and precision form one launch group; each phase of the step (push +
-// deposit, tile scan, scatter, field solve, step end) is ONE persistent launch over the
+// deposit + placement, tile scan, field solve, step end; the cell count, cell scan and
+// scatter on cell-sort steps) is ONE launch over the
 // (simulation, tile) work items of the whole group, pulled from a device counter.  The
 // step of all groups is captured once as a CUDA graph (and once more with the cell sort),
 // cached per exact list of sims.
