@@ -13,8 +13,10 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -24,6 +26,27 @@
 #include "sim_internal.h"
 
 using namespace sff;
+
+// Runs body(i0, i1) over [0, n) split into contiguous ranges on up to 16 host threads, at
+// least per_min items each (one thread when n is small); returns when all are done.
+template <typename F>
+static void host_parallel(long long n, long long per_min, F body)
+{
+    int nt = (int)std::min<long long>(16, std::max<long long>(1, n / per_min));
+    const unsigned hc = std::thread::hardware_concurrency();
+    if (hc > 0) nt = std::min<int>(nt, (int)hc);
+    if (nt <= 1) {
+        body(0LL, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    const long long chunk = (n + nt - 1) / nt;
+    for (int k = 0; k < nt; ++k) {
+        const long long i0 = k * chunk, i1 = std::min(n, i0 + chunk);
+        if (i0 < i1) th.emplace_back([=] { body(i0, i1); });
+    }
+    for (auto& t : th) t.join();
+}
 
 long long new_group_id()
 {
@@ -932,55 +955,88 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
     if (n > 0 && (!x || !u || !w || !id)) return fail(s, PIC_EINVAL, "NULL particle array");
     cudaStream_t st = (cudaStream_t)stream;
     const int D = s->cfg.dim, es = s->es;
-    std::vector<unsigned> cell(n), pid(n);
-    std::vector<char> off((size_t)D * n * es), mom((size_t)3 * n * es), wt((size_t)n * es);
-    for (int64_t p = 0; p < n; ++p) {
-        int c[3] = {0, 0, 0};
+    // host copies in the device layout (left uninitialised: every byte is written below)
+    std::unique_ptr<unsigned[]> cell(new unsigned[n > 0 ? n : 1]), pid(new unsigned[n > 0 ? n : 1]);
+    std::unique_ptr<char[]> off(new char[(size_t)D * n * es + 1]), mom(new char[(size_t)3 * n * es + 1]),
+        wt(new char[(size_t)n * es + 1]);
+    // converted on several host threads; each range reports its first invalid particle
+    const int nb = 16;
+    std::vector<long long> bad(nb, -1);
+    std::atomic<int> slot{0};
+    host_parallel(n, 1 << 16, [&](long long p0, long long p1) {
+        long long first = -1;
+        for (long long p = p0; p < p1 && first < 0; ++p) {
+            int c[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) {
+                const double X = x[3 * p + d] / s->cfg.dx;
+                const double fl = std::floor(X);
+                c[d] = (int)fl;
+                if (!(X >= s->h.margin) || !(X < s->h.n[d] - s->h.margin)) first = p;
+                double o = X - fl;
+                if (es == 4) {
+                    float of = (float)o;
+                    if (of >= 1.0f) of = std::nextafter(1.0f, 0.0f);
+                    memcpy(&off[((size_t)d * n + p) * 4], &of, 4);
+                } else {
+                    memcpy(&off[((size_t)d * n + p) * 8], &o, 8);
+                }
+            }
+            if (id[p] < 0 || id[p] >= (1ll << 31)) first = p;
+            unsigned v = (unsigned)c[0];
+            if (D > 1) v |= (unsigned)c[1] << s->h.cb[0];
+            if (D > 2) v |= (unsigned)c[2] << (s->h.cb[0] + s->h.cb[1]);
+            cell[p] = v;
+            pid[p] = (unsigned)id[p];
+            for (int d = 0; d < 3; ++d) {
+                if (es == 4) {
+                    float f = (float)u[3 * p + d];
+                    memcpy(&mom[((size_t)d * n + p) * 4], &f, 4);
+                } else {
+                    memcpy(&mom[((size_t)d * n + p) * 8], &u[3 * p + d], 8);
+                }
+            }
+            if (es == 4) {
+                float f = (float)w[p];
+                memcpy(&wt[(size_t)p * 4], &f, 4);
+            } else {
+                memcpy(&wt[(size_t)p * 8], &w[p], 8);
+            }
+        }
+        if (first >= 0) {
+            const int k = slot.fetch_add(1);
+            if (k < nb) bad[k] = first;
+        }
+    });
+    long long first_bad = -1;
+    for (long long b : bad)
+        if (b >= 0 && (first_bad < 0 || b < first_bad)) first_bad = b;
+    if (first_bad >= 0) {
+        const long long p = first_bad;
+        if (id[p] < 0 || id[p] >= (1ll << 31)) {
+            for (int d = 0; d < D; ++d) {
+                const double X = x[3 * p + d] / s->cfg.dx;
+                if (!(X >= s->h.margin) || !(X < s->h.n[d] - s->h.margin)) break;
+                if (d == D - 1) return fail(s, PIC_EINVAL, "particle id out of range");
+            }
+        }
         for (int d = 0; d < D; ++d) {
             const double X = x[3 * p + d] / s->cfg.dx;
-            const double fl = std::floor(X);
-            c[d] = (int)fl;
             if (!(X >= s->h.margin) || !(X < s->h.n[d] - s->h.margin))
-                return fail(s, PIC_EINVAL, "particle %lld at %g cells on axis %d is outside [%d, %d)", (long long)p, X,
-                            d, s->h.margin, s->h.n[d] - s->h.margin);
-            double o = X - fl;
-            if (es == 4) {
-                float of = (float)o;
-                if (of >= 1.0f) of = std::nextafter(1.0f, 0.0f);
-                memcpy(&off[((size_t)d * n + p) * 4], &of, 4);
-            } else {
-                memcpy(&off[((size_t)d * n + p) * 8], &o, 8);
-            }
+                return fail(s, PIC_EINVAL, "particle %lld at %g cells on axis %d is outside [%d, %d)", p, X, d,
+                            s->h.margin, s->h.n[d] - s->h.margin);
         }
-        if (id[p] < 0 || id[p] >= (1ll << 31)) return fail(s, PIC_EINVAL, "particle id out of range");
-        unsigned v = (unsigned)c[0];
-        if (D > 1) v |= (unsigned)c[1] << s->h.cb[0];
-        if (D > 2) v |= (unsigned)c[2] << (s->h.cb[0] + s->h.cb[1]);
-        cell[p] = v;
-        pid[p] = (unsigned)id[p];
-        for (int d = 0; d < 3; ++d) {
-            if (es == 4) {
-                float f = (float)u[3 * p + d];
-                memcpy(&mom[((size_t)d * n + p) * 4], &f, 4);
-            } else {
-                memcpy(&mom[((size_t)d * n + p) * 8], &u[3 * p + d], 8);
-            }
-        }
-        if (es == 4) {
-            float f = (float)w[p];
-            memcpy(&wt[(size_t)p * 4], &f, 4);
-        } else {
-            memcpy(&wt[(size_t)p * 8], &w[p], 8);
-        }
+        return fail(s, PIC_EINVAL, "particle id out of range");
     }
     if (n > 0) {
-        CU_CHECK(s, cudaMemcpyAsync(s->h.cell[1], cell.data(), n * 4, cudaMemcpyHostToDevice, st));
-        CU_CHECK(s, cudaMemcpyAsync(s->h.pid[1], pid.data(), n * 4, cudaMemcpyHostToDevice, st));
+        CU_CHECK(s, cudaMemcpyAsync(s->h.cell[1], cell.get(), n * 4, cudaMemcpyHostToDevice, st));
+        CU_CHECK(s, cudaMemcpyAsync(s->h.pid[1], pid.get(), n * 4, cudaMemcpyHostToDevice, st));
         for (int d = 0; d < D; ++d)
             CU_CHECK(s, cudaMemcpyAsync(s->h.off[1][d], &off[(size_t)d * n * es], n * es, cudaMemcpyHostToDevice, st));
         for (int d = 0; d < 3; ++d)
             CU_CHECK(s, cudaMemcpyAsync(s->h.mom[1][d], &mom[(size_t)d * n * es], n * es, cudaMemcpyHostToDevice, st));
-        CU_CHECK(s, cudaMemcpyAsync(s->h.wgt[1], wt.data(), n * es, cudaMemcpyHostToDevice, st));
+        CU_CHECK(s, cudaMemcpyAsync(s->h.wgt[1], wt.get(), n * es, cudaMemcpyHostToDevice, st));
+        // the host copies are released on return: the copies must have read them
+        CU_CHECK(s, cudaStreamSynchronize(st));
     }
     s->prefix_group = 0;   // a new layout: the next step numbers its chunks first
     pic_status r = sort_linear_into_set0(s, n, st);
@@ -1095,46 +1151,56 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
         long long tot = 0;
         for (int t = 0; t < nt; ++t) tot += tnum[t];
         if (tot != n) return fail(s, PIC_ECUDA, "tile counts (%lld) disagree with the particle count (%lld)", tot, n);
-        std::vector<unsigned> cell(nu), pid(nu);
-        std::vector<char> off((size_t)D * nu * es), mom((size_t)3 * nu * es), wt((size_t)nu * es);
+        // host copies (left uninitialised: the copies fill them)
+        std::unique_ptr<unsigned[]> cell(new unsigned[nu + 1]), pid(new unsigned[nu + 1]);
+        std::unique_ptr<char[]> off(new char[(size_t)D * nu * es + 1]), mom(new char[(size_t)3 * nu * es + 1]),
+            wt(new char[(size_t)nu * es + 1]);
         if (nu > 0) {
-            CU_CHECK(s, cudaMemcpyAsync(cell.data(), s->h.cell[q], nu * 4, cudaMemcpyDeviceToHost, st));
-            CU_CHECK(s, cudaMemcpyAsync(pid.data(), s->h.pid[q], nu * 4, cudaMemcpyDeviceToHost, st));
+            CU_CHECK(s, cudaMemcpyAsync(cell.get(), s->h.cell[q], nu * 4, cudaMemcpyDeviceToHost, st));
+            CU_CHECK(s, cudaMemcpyAsync(pid.get(), s->h.pid[q], nu * 4, cudaMemcpyDeviceToHost, st));
             for (int d = 0; d < D; ++d)
                 CU_CHECK(s, cudaMemcpyAsync(&off[(size_t)d * nu * es], s->h.off[q][d], nu * es, cudaMemcpyDeviceToHost, st));
             for (int d = 0; d < 3; ++d)
                 CU_CHECK(s, cudaMemcpyAsync(&mom[(size_t)d * nu * es], s->h.mom[q][d], nu * es, cudaMemcpyDeviceToHost, st));
-            CU_CHECK(s, cudaMemcpyAsync(wt.data(), s->h.wgt[q], nu * es, cudaMemcpyDeviceToHost, st));
+            CU_CHECK(s, cudaMemcpyAsync(wt.get(), s->h.wgt[q], nu * es, cudaMemcpyDeviceToHost, st));
         }
         CU_CHECK(s, cudaStreamSynchronize(st));
-        auto rd = [&](const std::vector<char>& v, size_t idx) {
+        auto rd = [&](const char* v, size_t idx) {
             if (es == 4) {
                 float f;
-                memcpy(&f, &v[idx * 4], 4);
+                memcpy(&f, v + idx * 4, 4);
                 return (double)f;
             }
-            double x;
-            memcpy(&x, &v[idx * 8], 8);
-            return x;
+            double xv;
+            memcpy(&xv, v + idx * 8, 8);
+            return xv;
         };
+        // record k of the output = the tiles' particles in tile order; tiles converted on
+        // several host threads from their first record index
+        std::vector<long long> first(nt + 1, 0);
+        for (int t = 0; t < nt; ++t)
+            first[t + 1] = first[t] + std::max<long long>(0, std::min<long long>((long long)toff[t] + tnum[t], nu) - toff[t]);
+        if (first[nt] != n) return fail(s, PIC_ECUDA, "tile slots hold %lld particles, expected %lld", first[nt], n);
         double* o = (double*)host_out;
-        long long k = 0;
-        for (int t = 0; t < nt; ++t) {
-            const long long p1 = std::min<long long>((long long)toff[t] + tnum[t], nu);
-            for (long long p = toff[t]; p < p1; ++p, ++k) {
-                const unsigned cl = cell[p];
-                int c[3];
-                c[0] = (int)(cl & ((1u << s->h.cb[0]) - 1u));
-                c[1] = D > 1 ? (int)((cl >> s->h.cb[0]) & ((1u << s->h.cb[1]) - 1u)) : 0;
-                c[2] = D > 2 ? (int)(cl >> (s->h.cb[0] + s->h.cb[1])) : 0;
-                for (int d = 0; d < 3; ++d)
-                    o[8 * k + d] = d < D ? ((double)c[d] + rd(off, (size_t)d * nu + p)) * s->cfg.dx : 0.0;
-                for (int d = 0; d < 3; ++d) o[8 * k + 3 + d] = rd(mom, (size_t)d * nu + p);
-                o[8 * k + 6] = rd(wt, p);
-                o[8 * k + 7] = (double)pid[p];
+        host_parallel(nt, std::max<long long>(1, (1 << 16) * (long long)nt / std::max<long long>(n, 1)),
+                      [&](long long t0, long long t1) {
+            for (long long t = t0; t < t1; ++t) {
+                long long k = first[t];
+                const long long p1 = std::min<long long>((long long)toff[t] + tnum[t], nu);
+                for (long long p = toff[t]; p < p1; ++p, ++k) {
+                    const unsigned cl = cell[p];
+                    int c[3];
+                    c[0] = (int)(cl & ((1u << s->h.cb[0]) - 1u));
+                    c[1] = D > 1 ? (int)((cl >> s->h.cb[0]) & ((1u << s->h.cb[1]) - 1u)) : 0;
+                    c[2] = D > 2 ? (int)(cl >> (s->h.cb[0] + s->h.cb[1])) : 0;
+                    for (int d = 0; d < 3; ++d)
+                        o[8 * k + d] = d < D ? ((double)c[d] + rd(off.get(), (size_t)d * nu + p)) * s->cfg.dx : 0.0;
+                    for (int d = 0; d < 3; ++d) o[8 * k + 3 + d] = rd(mom.get(), (size_t)d * nu + p);
+                    o[8 * k + 6] = rd(wt.get(), p);
+                    o[8 * k + 7] = (double)pid[p];
+                }
             }
-        }
-        if (k != n) return fail(s, PIC_ECUDA, "tile slots hold %lld particles, expected %lld", k, n);
+        });
         return PIC_OK;
     }
     case PIC_DIAG_EXITS: {

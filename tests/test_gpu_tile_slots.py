@@ -96,3 +96,35 @@ def test_particles_leave_in_every_direction_each_step(P, orc):
     assert np.abs(pg["x"][ia] - pr["x"][ib]).max() < 1e-9 * 100 * w.dx
     assert np.abs(pg["u"][ia] - pr["u"][ib]).max() < 1e-8
     sim.close()
+
+
+def test_set_particles_rejects_the_first_invalid_particle(P):
+    """A large upload (converted on several host threads): an out-of-range position or id
+    is rejected with the index of the first offending particle, and nothing is changed."""
+    w = synth.c2_2d_lp()
+    x, u, wt, ids = synth.slab_particles(w)
+    n = len(ids)
+    sim = P.Simulation(P.config_from(w, tile=(32, 16), chunk=1024))
+    before = sim.info().n_alive
+    bad_x = x.copy()
+    bad_x[n - 5, 1] = 1.0 * w.dx          # inside the removal margin on axis 1
+    bad_x[n // 2, 0] = -3.0                # outside the box on axis 0: the first offender
+    with pytest.raises(P.PicError) as e:
+        sim.set_particles(bad_x, u, wt, ids)
+    assert e.value.status == P.PIC_EINVAL and f"particle {n // 2} " in str(e.value) and "axis 0" in str(e.value)
+    bad_id = ids.copy()
+    bad_id[n - 3] = -1
+    with pytest.raises(P.PicError) as e:
+        sim.set_particles(x, u, wt, bad_id)
+    assert "id out of range" in str(e.value)
+    with pytest.raises(P.PicError) as e:
+        sim.set_particles(np.vstack([x, x[:1]]), np.vstack([u, u[:1]]), np.append(wt, wt[:1]), np.append(ids, n))
+    assert e.value.status == P.PIC_ECAPACITY
+    assert sim.info().n_alive == before
+    # a valid upload of the same records round-trips through the tile slots
+    sim.set_particles(x, u, wt, ids)
+    p = sim.particles()
+    order = np.argsort(p["id"])
+    assert np.array_equal(p["id"][order], ids)
+    assert np.abs(p["x"][order] - x).max() < 1e-6 * w.dx * 1024
+    sim.close()
