@@ -528,13 +528,10 @@ pic_status compute_rho_ion(pic_sim* s, cudaStream_t st)
     DevState ds;
     pic_status r = read_state(s, &ds, st);
     if (r != PIC_OK) return r;
-    CU_CHECK(s, cudaMemsetAsync(s->h.scratch, 0, sizeof(double) * s->nalloc_tot, st));
-    launch_charge(s->d, s->cfg.dim, s->cfg.precision, s->h.cap, s->h.scratch, st);
-    std::vector<double> tmp(s->nalloc_tot);
-    CU_CHECK(s, cudaMemcpyAsync(tmp.data(), s->h.scratch, sizeof(double) * s->nalloc_tot, cudaMemcpyDeviceToHost, st));
-    CU_CHECK(s, cudaStreamSynchronize(st));
-    for (double& v : tmp) v = -v;
-    CU_CHECK(s, cudaMemcpyAsync(s->h.rho_ion, tmp.data(), sizeof(double) * s->nalloc_tot, cudaMemcpyHostToDevice, st));
+    // immobile ions co-located with the electrons: rho_ion = -rho_e, deposited in place
+    CU_CHECK(s, cudaMemsetAsync(s->h.rho_ion, 0, sizeof(double) * s->nalloc_tot, st));
+    launch_charge(s->d, s->cfg.dim, s->cfg.precision, s->h.cap, s->h.rho_ion, st, -1.0);
+    CU_CHECK(s, cudaGetLastError());
     CU_CHECK(s, cudaStreamSynchronize(st));
     return PIC_OK;
 }

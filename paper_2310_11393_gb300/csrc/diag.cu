@@ -56,10 +56,10 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// charge density rho_e = -sum w S(x - x_node) on the primal nodes (array coordinates);
-// n: slots of a buffer set (as for the other particle diagnostics)
+// charge density scale * rho_e, rho_e = -sum w S(x - x_node), added on the primal nodes
+// (array coordinates); n: slots of a buffer set (as for the other particle diagnostics)
 template <int D, typename R>
-__global__ void k_charge(const SimDev* __restrict__ sim, long long n, double* __restrict__ rho)
+__global__ void k_charge(const SimDev* __restrict__ sim, long long n, double* __restrict__ rho, double scale)
 {
     const SimDev& S = *sim;
     const int par = S.st->parity;
@@ -85,7 +85,7 @@ __global__ void k_charge(const SimDev* __restrict__ sim, long long n, double* __
                 w[d][1] = w[d][2] = 0.0;
             }
         }
-        const double q = -(double)reinterpret_cast<const R*>(S.wgt[par])[p];
+        const double q = -scale * (double)reinterpret_cast<const R*>(S.wgt[par])[p];
         const int nk = D > 2 ? 3 : 1, nj = D > 1 ? 3 : 1;
         for (int k = 0; k < nk; ++k)
             for (int j = 0; j < nj; ++j)
@@ -282,13 +282,13 @@ static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<l
     } while (0)
 
 template <int D, typename R>
-static void charge_t(const SimDev* sim, long long n, double* rho, cudaStream_t s)
+static void charge_t(const SimDev* sim, long long n, double* rho, double scale, cudaStream_t s)
 {
-    if (n > 0) k_charge<D, R><<<grid_for(n), 256, 0, s>>>(sim, n, rho);
+    if (n > 0) k_charge<D, R><<<grid_for(n), 256, 0, s>>>(sim, n, rho, scale);
 }
-void launch_charge(const SimDev* sim, int dim, int prec, long long n_alive, double* rho, cudaStream_t s)
+void launch_charge(const SimDev* sim, int dim, int prec, long long n_slots, double* rho, cudaStream_t s, double scale)
 {
-    SFF_DISPATCH3(dim, prec, charge_t, sim, n_alive, rho, s);
+    SFF_DISPATCH3(dim, prec, charge_t, sim, n_slots, rho, scale, s);
 }
 
 template <int D, typename R>

@@ -75,7 +75,9 @@ void launch_scan_one(const SimDev* sim, int q, cudaStream_t s);
 void launch_next_slots(const SimDev* sim, int dim, int prec, int q, long long n, cudaStream_t s);
 
 // diagnostics
-void launch_charge(const SimDev* sim, int dim, int prec, long long n_alive, double* rho, cudaStream_t s);
+// adds scale * rho_e of the particles in the n_slots slots of the current set to rho
+void launch_charge(const SimDev* sim, int dim, int prec, long long n_slots, double* rho, cudaStream_t s,
+                   double scale = 1.0);
 void launch_gauss(const SimDev* sim, int dim, int prec, const int n[3], const double* rho, unsigned long long* out_bits,
                   cudaStream_t s);
 void launch_energy_fields(const SimDev* sim, int dim, int prec, const int n[3], double* acc2, cudaStream_t s);
