@@ -264,7 +264,8 @@ enum {
 };
 /* Writes diagnostic `kind` into host_out, which must hold at least the bytes the kind
  * needs (PIC_ECAPACITY otherwise; pic_info_get gives the counts).  Returns PIC_ETIMEOUT
- * if the device status word has the timeout bit, PIC_ENAN if an energy is not finite. */
+ * if the device status word has the timeout bit, PIC_ECAPACITY if it has the capacity
+ * bit, PIC_ENAN if an energy is not finite. */
 pic_status pic_diag(pic_sim* sim, int kind, void* host_out, size_t bytes, void* stream);
 
 /* Weighted electron histogram over kinetic energy gamma-1 in [0, e_max) (n_e bins) and
