@@ -400,12 +400,31 @@ def run_batch(args, rank=0, world=1, local_rank=0):
     if args.autotune > 0:
         pic.pic_autotune(c0, args.autotune, stream)
     tile, chunk = list(c0.tile), c0.chunk
+    chunk_of = {"plain": chunk, "batched": chunk}
 
-    def cfg_of(w):
-        return pic.config_from(w, tile=tile if args.autotune > 0 else None, chunk=chunk if args.autotune > 0 else 0)
+    def cfg_of(w, mode):
+        tuned = args.autotune > 0
+        return pic.config_from(w, tile=tile if tuned else None, chunk=chunk_of[mode] if tuned else 0)
+
+    if args.autotune > 0:
+        # the batched path's work-item size, measured on the batch itself (untimed set-up):
+        # the tuner's choice for one small member is not the best for the whole batch
+        trial = []
+        for ch in sorted({chunk, 1024, 2048}):
+            chunk_of["batched"] = ch
+            sims = [pic.Simulation(cfg_of(w, "batched"), stream=stream) for w in ws]
+            pic.pic_batch_step([s.h for s in sims], max(args.warmup, 2), stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pic.pic_batch_step([s.h for s in sims], 5, stream)
+            torch.cuda.synchronize()
+            trial.append((time.perf_counter() - t0, ch))
+            for s in sims:
+                s.close()
+        chunk_of["batched"] = min(trial)[1]
 
     for mode in ("plain", "batched"):
-        sims = [pic.Simulation(cfg_of(w), stream=stream) for w in ws]
+        sims = [pic.Simulation(cfg_of(w, mode), stream=stream) for w in ws]
         n0 = sum(s.info().n_alive for s in sims)
         # warm-up (graphs, attributes, batch graph capture)
         if mode == "plain":
@@ -437,7 +456,9 @@ def run_batch(args, rank=0, world=1, local_rank=0):
             "scaling": "strong", "parallelism": f"replicas x{world}, simulations round robin" if world > 1 else "single GPU",
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch2d_{len(ws_all)}", "sims": len(ws_all), "cells": cells,
-                       "tiles": {"push_tile": tile[:2], "chunk": chunk, "autotuned_on": ws[0].name}
+                       "tiles": {"push_tile": tile[:2], "chunk_plain": chunk_of["plain"],
+                                 "chunk_batched": chunk_of["batched"], "autotuned_on": ws[0].name,
+                                 "batched_chunk_measured_on": "the batch"}
                        if args.autotune > 0 else "defaults",
                        "particles": int(sum(w.n_particles for w in ws_all)),
                        "sample": f"steps {args.warmup}..{args.warmup + K} of each 500-step run"},
