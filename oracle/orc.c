@@ -1001,6 +1001,12 @@ void orc_step(orc_sim* s, int nsteps)
 }
 
 /* ---- diagnostics ---------------------------------------------------------------- */
+/* Total energies of Sec. 3.1 (the curves Eqs. L2_t / L2_t_cross compare), in the units of
+ * Table tab:units (energy density in n_c m c^2): EM = sum over the Yee points of
+ * (E^2 + B^2)/2 times the cell volume, for the scattered field and for scattered +
+ * incident field at the same points and time; kinetic = sum over electrons of
+ * w (gamma - 1) times the cell volume (w is the density one macro-electron carries), for
+ * the electrons in the box and for those that left it. */
 void orc_energies(const orc_sim* s, double out[4])
 {
     double vol = 1.0;

@@ -18,6 +18,10 @@
   (order 2, Sec. 3.1) -- exact discrete solution;
 * the cold-plasma Langmuir frequency w_p = sqrt(n_e) (Table tab:units);
 * first-order Mur faces absorb a 1D pulse;
+* the energy diagnostic: the EM energy of a sampled sin^2 pulse (scattered, and total with
+  the incident field on the grid) equals its closed-form integral, the kinetic energy of a
+  drifting plasma its integral, and a Langmuir oscillation trades one for the other at a
+  constant sum;
 * 1D total-field (boundary injection, case (i)) and scattered-field (case (ii)) runs
   agree and converge together (Sec. 3.1, Eqs. L2_t, L2_t_cross, Table tab:delta_E).
 """
@@ -365,3 +369,115 @@ def test_total_field_and_scattered_field_runs_agree(orc):
     (em1, k1), (em2, k2) = crosses
     assert em2 < 0.01 and k2 < 0.01            # within 1 % at dx = lambda/64
     assert em2 < em1 / 2.5                      # and converging with the cell size
+
+
+# ---- the energy diagnostic (Sec. 3.1: total energies E_EM = int (E^2 + B^2)/2 dV and
+# E_kin = int n (gamma - 1) dV in the units of Table tab:units, whose curves Eqs. L2_t and
+# L2_t_cross compare) pinned against closed forms --------------------------------------
+def _sin2_pulse_energy(a0, T):
+    """int (E_y^2 + B_z^2)/2 dx of the sin^2 plane-wave pulse E_y = B_z = a0 sin(xi - T)
+    sin^2(pi xi/(2T)) on [0, 2T], in closed form: with eta = xi - T the envelope is
+    cos^4(pi eta/(2T)) = 3/8 + cos(pi eta/T)/2 + cos(2 pi eta/T)/8 and sin^2 = (1 - cos 2eta)/2."""
+    def cc(a):   # int_{-T}^{T} cos(a eta) cos(2 eta) d eta
+        return math.sin(2 * T) if a == 0 else (math.sin((a - 2) * T) / (a - 2) + math.sin((a + 2) * T) / (a + 2))
+    env4 = 0.75 * T                                   # int cos^4
+    cross = 0.375 * cc(0.0) + 0.5 * cc(math.pi / T) + 0.125 * cc(2 * math.pi / T)
+    return a0 * a0 * 0.5 * (env4 - cross)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_field_energy_of_a_sampled_pulse_is_its_integral(orc, dim):
+    """A plane-wave pulse written onto the grid (E_y at its nodes, B_z half a cell further
+    along x, both at the same time): the EM energy is the closed-form integral times the
+    transverse length (a dropped 1/2, cell volume or component would fail), and the Yee
+    update in vacuum keeps it."""
+    a0, T, dxc = 1.7, 23.546, 2 * math.pi / 64
+    N = int(round(2 * math.pi * 16 / dxc))
+    ny = 8 if dim == 2 else 1
+    c = cfg(orc, dim=dim, n=(N, ny, 1), dx=dxc, dt=0.95 * dxc / math.sqrt(dim), field_bc=orc.BC_PERIODIC)
+    sim = orc.Sim(c)
+    ext = sim.ext
+    xs = 10.0
+    f = lambda x: np.where((x > xs) & (x < xs + 2 * T), a0 * np.sin(x - xs - T) * np.sin(np.pi * (x - xs) / (2 * T)) ** 2, 0.0)
+    F = np.zeros((9, ext[2], ext[1], ext[0]))
+    F[1, :, :, :] = f(np.arange(ext[0]) * dxc)[None, None, :]
+    F[5, :, :, :] = f((np.arange(ext[0]) + 0.5) * dxc)[None, None, :]
+    sim.set_fields(F)
+    exact = _sin2_pulse_energy(a0, T) * (ny * dxc if dim == 2 else 1.0)
+    e = sim.energies()
+    assert abs(e[0] / exact - 1) < 1e-10, (e[0], exact)
+    assert e[2] == 0.0 and e[3] == 0.0
+    sim.step(200)
+    assert abs(sim.energies()[0] / exact - 1) < 1e-5
+
+
+def test_incident_pulse_energy_on_the_grid(orc):
+    """Scattered-field run without plasma: the scattered energy stays 0 and the total-field
+    energy (scattered + incident at the grid points) is the incident pulse's closed-form
+    energy once the whole pulse is inside the box (pins the incident term's stagger and
+    time)."""
+    a0, T, dxc = 1.3, 23.546, 2 * math.pi / 64
+    N = 900
+    dt = 0.95 * dxc
+    c = cfg(orc, n=(N, 1, 1), dx=dxc, dt=dt, beam=orc.BEAM_PLANE, envelope=orc.ENV_SIN2, a0=a0, duration=T,
+            focus=(0.0, 0, 0))
+    sim = orc.Sim(c)
+    sim.step(int(round((2 * T + 8.0) / dt)))      # pulse in [~8, 2T + 8]
+    e = sim.energies()
+    assert e[0] == 0.0
+    assert abs(e[1] / _sin2_pulse_energy(a0, T) - 1) < 1e-10, e
+
+
+def test_kinetic_energy_of_a_drifting_plasma(orc):
+    """Electrons evenly spread over a periodic 2D box with u_x = u0 sin(k x): the kinetic
+    energy is n_e int (gamma - 1) dA, i.e. n_e L_y int_0^L (sqrt(1 + u0^2 sin^2 kx) - 1) dx
+    (pins the macro-weight, gamma - 1 and the cell area)."""
+    from scipy.integrate import quad
+
+    N, ny, dx, ne, ppc, u0 = 64, 4, 0.1, 0.03, 8, 0.8
+    c = cfg(orc, dim=2, n=(N, ny, 1), dx=dx, dt=0.06, field_bc=orc.BC_PERIODIC)
+    sim = orc.Sim(c)
+    L, Ly = N * dx, ny * dx
+    npx = N * ppc
+    xs = (np.arange(npx) + 0.5) * (L / npx)
+    X = np.zeros((npx * ny, 3)); U = np.zeros((npx * ny, 3))
+    for j in range(ny):
+        X[j * npx:(j + 1) * npx, 0] = xs
+        X[j * npx:(j + 1) * npx, 1] = (j + 0.5) * dx
+        U[j * npx:(j + 1) * npx, 0] = u0 * np.sin(2 * math.pi * xs / L)
+    # each particle stands for the density n_e over a cell area: ppc per cell (N*ny cells)
+    sim.set_particles(X, U, np.full(npx * ny, ne / ppc), np.arange(npx * ny))
+    k = 2 * math.pi / L
+    want = ne * Ly * quad(lambda x: math.sqrt(1 + (u0 * math.sin(k * x)) ** 2) - 1, 0, L, limit=200)[0]
+    assert abs(sim.energies()[2] / want - 1) < 1e-10
+
+
+def test_langmuir_energy_exchange(orc):
+    """Cold periodic plasma with a velocity perturbation: kinetic energy turns into field
+    energy and back (a Langmuir oscillation) while their sum stays within 1e-3 of itself,
+    the deviation shrinking with dt: fixes the relative normalisation of the two energies
+    (u lives at half steps: the kinetic energy at step n is the mean of its values at
+    n -/+ 1/2)."""
+    N, dx, ne, ppc = 128, 0.1, 0.04, 8
+    var = []
+    for dt in (0.095, 0.0475):
+        c = cfg(orc, n=(N, 1, 1), dx=dx, dt=dt, field_bc=orc.BC_PERIODIC)
+        sim = orc.Sim(c)
+        npart = N * ppc
+        x = (np.arange(npart) + 0.5) * (dx / ppc)
+        X = np.zeros((npart, 3)); X[:, 0] = x
+        U = np.zeros((npart, 3)); U[:, 0] = 1e-2 * np.sin(2 * math.pi * x / (N * dx))
+        sim.set_particles(X, U, np.full(npart, ne / ppc), np.arange(npart))
+        em, kin = [], []
+        for _ in range(int(round(300 * 0.095 / dt))):   # about 1.4 plasma periods
+            sim.step(1)
+            e = sim.energies()
+            em.append(e[0]); kin.append(e[2])
+        em, kin = np.array(em), np.array(kin)
+        tot = em[:-1] + 0.5 * (kin[1:] + kin[:-1])
+        scale = tot.mean()
+        assert em.max() > 0.99 * scale and em.min() < 1e-3 * scale        # full exchange
+        assert kin.max() > 0.99 * scale and kin.min() < 1e-3 * scale
+        var.append((tot.max() - tot.min()) / scale)
+    assert var[0] < 1e-3
+    assert var[1] < 0.7 * var[0]            # shrinks with dt (measured: first order)
