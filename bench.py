@@ -3,16 +3,22 @@
 
 One step = push + incident-field evaluation + gather + Boris + Esirkepov deposit for every
 macro-electron, the particle re-sort by tile, and the Yee update of the scattered field.
-Default workload: the 2D tightly focused LP case (1024 x 1024 cells, dx = lambda/32, LP pulse
-w0 = lambda, a0 = 10, 5 fs, 512 x 512-cell slab at 0.05 n_c with 8 ppc = 2 097 152 electrons).
-Metric: particle-pushes/s (each push includes the incident-field evaluation and the deposit).
+Default workload: the largest single-GPU configuration, the 3D tightly focused RP case
+(512 x 256 x 256 cells, dx = lambda/24, RP pulse w0 = 0.7 lambda, a0 = 20, 5 fs,
+256 x 128 x 128-cell slab at 0.01 n_c with 4 ppc = 16 777 216 electrons).  The K timed steps
+are the window of the run centred on the step at which the pulse peak crosses the focus
+(the simulation is first advanced to the window's start, untimed); --window start times
+the first K steps instead.  Metric: particle-pushes/s (each push includes the
+incident-field evaluation and the deposit).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2d|3d|1d]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 3d|2d|1d]
 
-N > 1 (torchrun, one process per GPU): every rank advances its own replica of the workload
+N > 1: one process per GPU (when WORLD_SIZE is not set, bench.py starts the N ranks itself
+under torch.distributed.run); every rank advances its own replica of the workload
 (independent simulations: no data-path collective), timing is max over ranks and the value
-sums all ranks' pushes (weak scaling).  --impl reference times the FP64 CPU oracle on the
-host cores on a bounded sample of the same workload.
+sums all ranks' pushes (weak scaling).  --impl reference times the FP64 CPU oracle on all
+host cores (one single-threaded oracle process per core, each on its own seeded sample box
+of the same workload).
 """
 import argparse
 import json
@@ -40,9 +46,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (default: the workload's full run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["1d", "2d", "3d", "2d_gauss", "batch", "serve"])
+    ap.add_argument("--workload", default="3d", choices=["1d", "2d", "3d", "2d_gauss", "batch", "serve"])
+    ap.add_argument("--window", default="focus", choices=["focus", "start"],
+                    help="timed steps centred on the pulse crossing the focus (default) or from t = 0")
     ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
     ap.add_argument("--tile", default="", help="particle tile, e.g. 16,8,4 (skips the autotuner's tile search)")
+    ap.add_argument("--chunk", type=int, default=0, help="particles per push work item (skips its autotuning)")
     ap.add_argument("--autotune", type=int, default=10,
                     help="trial steps per candidate of the tile/work-item autotuner before timing (0: defaults)")
     ap.add_argument("--incident", default="particle", choices=["particle", "grid"],
@@ -185,6 +194,20 @@ def job_totals(pushes, secs, world, device=None):
     return float(p.item()), float(t.item())
 
 
+def window_start(w, k, mode):
+    """First timed step: the K-step window centred on the step at which the pulse peak
+    crosses the focus (focused beams: t_focus; plane wave: the envelope centre at the slab
+    centre), kept inside the run; 0 for mode "start" or when K covers the run."""
+    if mode == "start" or k >= w.steps:
+        return 0
+    if w.beam == synth.BEAM_PLANE:
+        t_c = w.duration + 0.5 * (w.slab_lo[0] + w.slab_hi[0]) * w.dx - w.focus[0]
+    else:
+        t_c = w.t_focus
+    centre = int(round(t_c / w.dt))
+    return max(0, min(w.steps - k, centre - k // 2))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -195,9 +218,10 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = workload(args.workload)
     tile = [int(v) for v in args.tile.split(",")] if args.tile else None
-    cfg = pic.config_from(w, tile=tile, sort_every=args.sort_every)
+    cfg = pic.config_from(w, tile=tile, sort_every=args.sort_every, chunk=args.chunk)
     stream = torch.cuda.current_stream(dev).cuda_stream
     alloc = pic.torch_allocator(local_rank)
+    s0 = window_start(w, args.steps, args.window)
     # tile and work-item size: measured by the autotuner (untimed set-up)
     tune = {"trial_steps": args.autotune}
     if args.autotune > 0:
@@ -209,13 +233,18 @@ def run_ours(args, rank, world, local_rank):
     tune["chunk"] = prm.chunk
     tune["field_solver_tile"] = list(prm.yee_tile)[: w.dim]
     tune["cell_sort_every"] = prm.sort_every
+    # measured issue rates of this GPU (the fused push's arithmetic roofline)
+    pk = pic.pic_probe_peaks(stream)
     # warm-up: W steps on a throw-away instance (clocks, caches, graph, launch attributes)
     warm = pic.Simulation(cfg, allocator=alloc, stream=stream)
     warm.step(args.warmup)
     torch.cuda.synchronize()
     warm.close()
-    # the job: a fresh simulation (inputs resident in HBM) advanced K steps from t = 0
+    # the job: a fresh simulation (inputs resident in HBM), advanced untimed to the window's
+    # first step, then K timed steps
     sim = pic.Simulation(cfg, allocator=alloc, stream=stream)
+    if s0:
+        sim.step(s0)
     torch.cuda.synchronize()
     n_a = sim.info().n_alive
     if world > 1:
@@ -230,27 +259,34 @@ def run_ours(args, rank, world, local_rank):
     e1.record(torch.cuda.current_stream(dev))
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clk = clocks.stop()
     n_b = sim.info().n_alive
     pushes = 0.5 * (n_a + n_b) * args.steps
     tot_pushes, t_max = job_totals(pushes, secs, world, dev)
-    if world > 1:
-        torch.distributed.barrier()
     info = sim.info()
     sim.close()
-    # live per-kernel timing over the same window: another fresh instance, K steps from t = 0,
-    # CUDA events between the kernels of every step
+    # live per-kernel timing over the same window: another fresh instance advanced to the
+    # same step, then K steps with CUDA events between the kernels of every step
     psim = pic.Simulation(cfg, allocator=alloc, stream=stream)
+    if s0:
+        psim.step(s0)
+    snap = None
+    if not args.no_e2e:      # the state at the window's start, for the end-to-end run
+        snap = (psim.particles(), psim.fields())
     nsteps_prof = args.steps if args.profile_steps <= 0 else min(args.steps, args.profile_steps)
     nwin = 10 if nsteps_prof >= 10 else 1
     prof = np.zeros(5)
     windows = []
     done = 0
+    n_p0 = psim.info().n_alive
     for k in range(nwin):
         m = nsteps_prof * (k + 1) // nwin - done
         pw = pic.pic_profile_step(psim.h, m, stream)
         prof += pw
-        windows.append({"steps": [done, done + m], "n_alive": int(psim.info().n_alive),
+        windows.append({"steps": [s0 + done, s0 + done + m], "n_alive": int(psim.info().n_alive),
                         "ms_per_step": [round(x / m * 1e3, 4) for x in pw]})
         done += m
     n_c = psim.info().n_alive
@@ -259,24 +295,32 @@ def run_ours(args, rank, world, local_rank):
     yee_s = prof[3] / nsteps_prof
 
     hbm, sm_max, src = peaks()
-    npush = 0.5 * (n_a + n_c)
+    npush = 0.5 * (n_p0 + n_c)
     fl = flops_per_push(w) * npush
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s: SMs x FP32 lanes x FMA x clock
-    alu_frac = fl / push_s / 1e12 / fp32_peak
+    es = 4 if w.precision == synth.FP32 else 8
+    if es == 4:
+        alu_peak, alu_name = pk.fp32_tflops, "FP32"
+    else:
+        alu_peak, alu_name = pk.fp64_tflops, "FP64"
+    alu_frac = fl / push_s / 1e12 / alu_peak
     by = bytes_per_push(w) * npush
     hbm_frac = by / push_s / 1e9 / hbm
-    es = 4 if w.precision == synth.FP32 else 8
     cells = w.n_cells
     yee_bytes = cells * (9 * es + 6 * es + 3 * es)           # read E, B, J; write E, B; clear J
     kname = "k_push<%d,%s>" % (w.dim, "float" if es == 4 else "double")
     traffic = PROFILED_TRAFFIC.get((w.name, kname))
-    roof = {"bound": "alu", "achieved": round(fl / push_s / 1e12, 3), "peak": round(fp32_peak, 2),
+    roof = {"bound": "alu", "achieved": round(fl / push_s / 1e12, 3), "peak": round(alu_peak, 2),
             "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic[0] if traffic else None,
             "traffic_source": traffic[1] if traffic else None, "kernel": kname,
-            "peak_source": f"SM count x FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
+            "peak_source": f"measured: {alu_name} FMA-chain probe (pic_probe_peaks) over {pk.sms} SMs at "
+                           f"{pk.sm_clock_mhz:.0f} MHz",
+            "flop_per_push": flops_per_push(w),
+            "probe": {"sms": pk.sms, "fp32_tflops": round(pk.fp32_tflops, 2), "fp64_tflops": round(pk.fp64_tflops, 3),
+                      "sfu_gops": round(pk.sfu_gops, 1), "sm_clock_mhz": round(pk.sm_clock_mhz, 1),
+                      "fp32_flop_per_clk_sm": round(pk.fp32_flop_per_clk_sm, 1)},
             "push_ms": round(push_s * 1e3, 4),
-            "hbm_view": {"achieved_gbs": round(by / push_s / 1e9, 1), "peak_gbs": hbm, "frac": round(hbm_frac, 4),
-                         "bytes_per_push": round(bytes_per_push(w), 2)},
+            "hbm_view": {"achieved_gbs": round(by / push_s / 1e9, 1), "peak_gbs": hbm, "peak_source": src,
+                         "frac": round(hbm_frac, 4), "bytes_per_push": round(bytes_per_push(w), 2)},
             "yee": {"ms": round(yee_s * 1e3, 4), "achieved_gbs": round(yee_bytes / yee_s / 1e9, 1),
                     "frac_of_hbm": round(yee_bytes / yee_s / 1e9 / hbm, 4), "bytes_per_cell": 18 * es},
             "phases_ms": [round(x / nsteps_prof * 1e3, 4) for x in prof],
@@ -284,14 +328,17 @@ def run_ours(args, rank, world, local_rank):
             "windows": windows}
 
     e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, w, cfg, pic, torch, dev, stream, alloc)
+    if snap is not None:
+        e2e = run_e2e(args, w, cfg, pic, torch, stream, alloc, snap, s0)
     out = {"metric": METRIC, "value": tot_pushes / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if es == 4 else "f64", "data": "synthetic",
            "config": {"workload": w.name, "dim": w.dim, "grid": list(w.n[: w.dim]), "particles": w.n_particles,
                       "ppc": w.ppc, "beam": {1: "plane", 2: "LP", 3: "RP", 5: "Gaussian 2D"}[w.beam],
                       "precision": "fp32 body, fp64 phase" if es == 4 else "fp64",
+                      "window": {"mode": args.window, "steps": [s0, s0 + args.steps], "run_steps": w.steps,
+                                 "focus_step": int(round(w.t_focus / w.dt)) if w.beam != synth.BEAM_PLANE else None,
+                                 "advanced_untimed": s0},
                       "cell_updates_per_s": cells * args.steps * world / t_max,
                       "l2": "inputs larger than L2 (device state %.2f GB > 129 MB)" % (info.params.device_bytes / 1e9),
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "tiles": tune},
@@ -303,44 +350,109 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_e2e(args, w, cfg, pic, torch, dev, stream, alloc):
-    """Through the C-ABI with HOST buffers: the initial particle state goes host -> device, the
-    steps run, the energies and every particle's state come back device -> host."""
-    x, u, wt, ids = synth.slab_particles(w)
+def run_e2e(args, w, cfg, pic, torch, stream, alloc, snap, s0):
+    """Through the C-ABI with HOST buffers: the state at the window's first step (every
+    particle and the six field components, as a user restores a checkpoint) goes host ->
+    device, the K steps run, the energies and every particle's state come back device ->
+    host, all inside the timed region."""
+    parts, fields = snap
+    x, u, wt, ids = parts["x"], parts["u"], parts["w"], parts["id"]
     sim = pic.Simulation(cfg, allocator=alloc, stream=stream)
     n = len(ids)
     es = 4 if w.precision == synth.FP32 else 8
-    h2d = n * (4 + 4 + w.dim * es + 3 * es + es)
-    d2h = n * (4 + 4 + w.dim * es + 3 * es + es) + 64
+    rec = 4 + 4 + w.dim * es + 3 * es + es          # cell, id, offsets, momenta, weight
+    ext = [w.n[d] + 1 if d < w.dim else 1 for d in range(3)]
+    npts = ext[0] * ext[1] * ext[2]
+    h2d = n * rec + 6 * npts * es
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.set_particles(x, u, wt, ids)
+    sim.set_fields(fields)
+    pic.pic_set_step(sim.h, s0, stream)
     sim.step(args.steps)
     en = sim.energies()
-    parts = sim.particles()
+    out = sim.particles()
     t1 = time.perf_counter()
-    n_end = len(parts["id"])
+    n_end = len(out["id"])
+    d2h = n_end * rec + 64
     sim.close()
     pushes = 0.5 * (n + n_end) * args.steps
     return {"value": pushes / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d / args.steps),
             "d2h_bytes_per_step": int(d2h / args.steps), "seconds": t1 - t0,
+            "what": f"restore the state at step {s0} from host arrays (particles, E and B), {args.steps} steps, "
+                    "energies and every particle back to the host",
             "energies": [float(v) for v in en[:4]]}
 
 
-def cpu_baseline(w, nsteps):
-    """The oracle as it stands, single-threaded, on the full workload for nsteps steps."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(job):
+    """One single-threaded oracle process: the sample workload with its own seed, `warm`
+    untimed steps, then `steps` timed steps; returns (pushes, seconds)."""
+    w, warm, steps = job
+    sys.path.insert(0, ROOT)
     import oracle
 
     sim = oracle.Sim(oracle.config_from(w))
+    if warm:
+        sim.step(warm)
     n0 = sim.num_particles()
     t0 = time.perf_counter()
-    sim.step(nsteps)
+    sim.step(steps)
     t1 = time.perf_counter()
     n1 = sim.num_particles()
-    pushes = 0.5 * (n0 + n1) * nsteps
-    return {"value": pushes / (t1 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"full {w.name} workload ({n0} electrons), {nsteps} steps from t = 0, FP64, 1 thread",
-            "seconds": t1 - t0}
+    return 0.5 * (n0 + n1) * steps, t1 - t0
+
+
+def oracle_all_cores(w, warm, steps):
+    """The oracle as it stands on every host core at once: nproc single-threaded processes
+    (spawned), each on its own seeded copy of the sample box w.  Returns (pushes/s of the
+    whole host, per-process pushes/s, cores)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    jobs = [(w.with_(seed=w.seed + 7919 * k), warm, steps) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    pushes = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return pushes / secs, [r[0] / r[1] for r in res], cores
+
+
+def cpu_baseline(w, nsteps=None):
+    """The oracle on all host cores: one single-threaded process per core, each advancing
+    its own seeded sample box of the workload (same physics and cell size) for nsteps
+    steps from t = 0."""
+    ws, f = reference_sample(w)
+    if nsteps is None:
+        nsteps = max(2, min(40, int(1.5e6 / max(ws.n_particles, 1))))
+    v, per, cores = oracle_all_cores(ws, 0, nsteps)
+    what = f"full {w.name} workload" if f == 1 else f"{w.name} box divided by {f} per axis"
+    return {"value": v, "unit": UNIT, "cores": cores, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "kind": "oracle",
+            "sample": f"{cores} single-threaded oracle processes at once, each on its own seeded copy of the "
+                      f"{what} ({ws.n_particles} electrons), {nsteps} steps from t = 0, FP64",
+            "per_core_pushes_per_s": round(float(np.mean(per)), 1)}
 
 
 def reference_sample(w, max_particles=80_000):
@@ -356,26 +468,19 @@ def reference_sample(w, max_particles=80_000):
 def run_reference(args, rank, world):
     full = workload(args.workload)
     w, f = reference_sample(full)
-    import oracle
-
-    oracle.build()
-    sim = oracle.Sim(oracle.config_from(w))
-    sim.step(args.warmup)
-    n0 = sim.num_particles()
-    t0 = time.perf_counter()
-    sim.step(args.steps)
-    t1 = time.perf_counter()
-    n1 = sim.num_particles()
-    v = 0.5 * (n0 + n1) * args.steps / (t1 - t0)
+    v, per, cores = oracle_all_cores(w, args.warmup, args.steps)
     what = f"full {w.name} workload" if f == 1 else f"{full.name} box divided by {f} per axis ({w.n_particles} electrons)"
-    cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": f"{what}, {args.steps} steps after {args.warmup} warm-up steps, FP64, 1 thread"}
+    cb = {"value": v, "unit": UNIT, "cores": cores, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+          "kind": "oracle",
+          "sample": f"{cores} single-threaded oracle processes at once, each on its own seeded copy of the {what}, "
+                    f"{args.steps} steps after {args.warmup} warm-up steps, FP64",
+          "per_core_pushes_per_s": round(float(np.mean(per)), 1)}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": (t1 - t0) / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": cores * w.n_particles / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": full.name, "dim": full.dim, "grid": list(full.n[: full.dim]),
                        "particles": full.n_particles, "sample_grid": list(w.n[: w.dim]),
-                       "sample_particles": w.n_particles},
+                       "sample_particles": w.n_particles, "sample_copies": cores},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -534,8 +639,23 @@ def run_serve(args):
                       "makespan_s": plain_secs}, "check": check}
 
 
+def relaunch_ranks(args):
+    """--gpus N > 1 without a launcher: start N ranks of this command under
+    torch.distributed.run on this node (127.0.0.1) and return its exit code."""
+    import socket
+
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_ranks(args))
     global SCALE, INCIDENT_GRID
     SCALE = max(1, args.scale)
     INCIDENT_GRID = 1 if args.incident == "grid" else 0
@@ -569,7 +689,7 @@ def main():
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
         run_cb = world == 1 and not args.no_cpu_baseline
-        out["cpu_baseline"] = cpu_baseline(workload(args.workload), 4) if run_cb else None
+        out["cpu_baseline"] = cpu_baseline(workload(args.workload)) if run_cb else None
         print(json.dumps(out))
     if world > 1:
         import torch

@@ -270,7 +270,9 @@ pic_status pic_diag(pic_sim* sim, int kind, void* host_out, size_t bytes, void* 
 
 /* Weighted electron histogram over kinetic energy gamma-1 in [0, e_max) (n_e bins) and
  * angle from the +x (propagation) axis in [0, pi] (n_a bins); electrons in the box plus
- * exits.  HOST output: double[n_e * n_a], angle fastest.  Synchronous. */
+ * exits.  HOST output: double[n_e * n_a], angle fastest.  Runs on the simulation's device
+ * (made current for the call).  Synchronous.  Returns PIC_ETIMEOUT / PIC_ECAPACITY for the
+ * device status word's timeout / capacity bits, as pic_diag. */
 pic_status pic_histogram(pic_sim* sim, int n_e, double e_max, int n_a, double* host_out, void* stream);
 
 /* Same weighted energy-angle histogram as pic_histogram, for callers that must not allocate
@@ -283,7 +285,9 @@ pic_status pic_histogram(pic_sim* sim, int n_e, double e_max, int n_a, double* h
  * that first call before any stream capture.  Every call clears the bins it uses and then
  * leaves its result in the array; calls that overlap on the GPU (different streams or host
  * threads) share the array and race, so serialise them.  n_e * n_a > PIC_HIST_STATIC_MAX_BINS
- * is rejected with PIC_EINVAL.  HOST output double[n_e * n_a], angle fastest.  Synchronous.
+ * is rejected with PIC_EINVAL.  HOST output double[n_e * n_a], angle fastest.  Runs on the
+ * simulation's device (made current for the call, including the first call's look-up); the
+ * status word is read as pic_diag reads it (PIC_ETIMEOUT, PIC_ECAPACITY).  Synchronous.
  * (No counterpart in the paper: this is an interface for constrained callers.) */
 #define PIC_HIST_STATIC_MAX_BINS 16384
 pic_status pic_histogram_static(pic_sim* sim, int n_e, double e_max, int n_a, double* host_out, void* stream);
@@ -333,6 +337,38 @@ pic_status pic_serve_poll(pic_server* srv, uint64_t ticket, pic_result* out);
 double pic_serve_clock(const pic_server* srv);
 /* Finishes running requests, stops the thread, frees everything. */
 pic_status pic_serve_close(pic_server* srv);
+
+/* ---- test aid (no counterpart in the paper) --------------------------------------- */
+/* Fault injection for the bounded device waits, without faulting the GPU: block `block` of
+ * the single-simulation tile scan (which scans 4096 particle tiles per block and chains the
+ * blocks by decoupled look-back) stops publishing its totals, so the blocks after it poll
+ * its flag `spins` times (default 2^22, about a second), give up, set PIC_FLAG_TIMEOUT in
+ * the status word and take a zero prefix, which keeps every later offset inside the
+ * particle arrays (the particle layout is then wrong, and the next synchronous call returns
+ * PIC_ETIMEOUT).  block = -1 restores publishing.  Only simulations with more than 4096
+ * particle tiles use the multi-block scan.  Synchronous.  Errors: PIC_EINVAL (spins < 1),
+ * PIC_ECUDA. */
+pic_status pic_test_hold_scan(pic_sim* sim, int block, int spins);
+
+/* ---- measurement aid (no counterpart in the paper) -------------------------------- */
+/* Issue rates of the current device measured with CUDA events over all SMs: dependency
+ * chains of FP32 fused multiply-adds (8 independent chains per thread, the loop unrolled
+ * 16 times), of FP64 fused multiply-adds and of the special-function unit's approximate
+ * sine.  fp32_tflops counts an FMA as two operations; sfu_gops counts one per sine.  The SM
+ * clock is clock64() cycles of the longest block over the event time of the FP32 probe,
+ * and fp32_flop_per_clk_sm the FP32 rate per SM and clock it implies.  The fused push's
+ * transcendental-heavy closed form is bound by these rates rather than by HBM, so they
+ * are its roofline.  About 0.2 s of GPU time; allocates 64 bytes plus 8 per block with
+ * cudaMalloc.  Synchronous on `stream`.  Errors: PIC_ENODEV, PIC_ENOMEM, PIC_ECUDA. */
+typedef struct {
+    int32_t sms;             /* streaming multiprocessors of the device */
+    double fp32_tflops;
+    double fp64_tflops;
+    double sfu_gops;
+    double sm_clock_mhz;
+    double fp32_flop_per_clk_sm;
+} pic_peaks;
+pic_status pic_probe_peaks(pic_peaks* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libsffpic.so")
-SOURCES = ["push.cu", "yee.cu", "diag.cu", "capi.cu", "batch.cu", "serve.cu", "tune.cu"]
+SOURCES = ["push.cu", "yee.cu", "diag.cu", "capi.cu", "batch.cu", "serve.cu", "tune.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "-I", os.path.join(HERE, "..", "include")]

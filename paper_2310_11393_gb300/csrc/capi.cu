@@ -667,6 +667,8 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     s->sort_every = L.sort_every;
     s->pcap = L.cap;
     h.nscanblk = (L.nptiles + 4095) / 4096;
+    h.scan_spins = 1 << 22;      // about a second of polls of a predecessor's flag
+    h.scan_hold = -1;
     h.scanflags = (unsigned long long*)A.take((size_t)h.nscanblk * 8);
     h.scanticket = (int*)A.take(4);
     h.exits = (double*)A.take((size_t)L.max_exits * EXIT_DOUBLES * 8);
@@ -943,6 +945,19 @@ pic_status pic_set_step(pic_sim* s, int64_t step, void* stream)
     return write_state(s, ds, st);
 }
 
+pic_status pic_test_hold_scan(pic_sim* s, int block, int spins)
+{
+    if (!s || spins < 1) return fail(s, PIC_EINVAL, "bad argument");
+    s->h.scan_hold = block;
+    s->h.scan_spins = spins;
+    // the two fields of the device descriptor (read by every later launch of the step graph)
+    const size_t o = offsetof(SimDev, scan_spins);
+    static_assert(offsetof(SimDev, scan_hold) == offsetof(SimDev, scan_spins) + sizeof(int), "layout");
+    CU_CHECK(s, cudaMemcpy(reinterpret_cast<char*>(s->d) + o, reinterpret_cast<const char*>(&s->h) + o, 2 * sizeof(int),
+                           cudaMemcpyHostToDevice));
+    return PIC_OK;
+}
+
 pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const double* u, const double* w,
                              const int64_t* id, void* stream)
 {
@@ -1056,29 +1071,32 @@ pic_status pic_set_fields(pic_sim* s, const double* fields, void* stream)
     const int ext[3] = {s->h.n[0] + 1, D > 1 ? s->h.n[1] + 1 : 1, D > 2 ? s->h.n[2] + 1 : 1};
     const long long ne = (long long)ext[0] * ext[1] * ext[2];
     std::vector<char> buf((size_t)6 * s->nalloc_tot * s->es, 0);
-    for (int comp = 0; comp < 6; ++comp) {
-        const int c = comp % 3;
-        for (int k = 0; k < ext[2]; ++k)
-            for (int j = 0; j < ext[1]; ++j)
-                for (int i = 0; i < ext[0]; ++i) {
-                    const int g[3] = {i, j, k};
-                    bool has = true;
-                    for (int d = 0; d < D; ++d) {
-                        const bool stag = comp < 3 ? (d == c) : (d != c);
-                        if (stag && g[d] > s->h.n[d] - 1) has = false;
-                    }
-                    if (!has) continue;
-                    const double v = fields[comp * ne + ((long long)k * ext[1] + j) * ext[0] + i];
-                    const long long o = comp * s->nalloc_tot + (long long)(D > 2 ? k + G : 0) * s->h.sz +
-                                        (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + G);
-                    if (s->es == 4) {
-                        float f = (float)v;
-                        memcpy(&buf[o * 4], &f, 4);
-                    } else {
-                        memcpy(&buf[o * 8], &v, 8);
-                    }
+    // rows (comp, k, j) of the host array converted on up to 16 host threads
+    const long long nrows = 6LL * ext[2] * ext[1];
+    host_parallel(nrows, 256, [&](long long r0, long long r1) {
+        for (long long r = r0; r < r1; ++r) {
+            const int j = (int)(r % ext[1]), k = (int)((r / ext[1]) % ext[2]), comp = (int)(r / ((long long)ext[1] * ext[2]));
+            const int c = comp % 3;
+            for (int i = 0; i < ext[0]; ++i) {
+                const int g[3] = {i, j, k};
+                bool has = true;
+                for (int d = 0; d < D; ++d) {
+                    const bool stag = comp < 3 ? (d == c) : (d != c);
+                    if (stag && g[d] > s->h.n[d] - 1) has = false;
                 }
-    }
+                if (!has) continue;
+                const double v = fields[comp * ne + ((long long)k * ext[1] + j) * ext[0] + i];
+                const long long o = comp * s->nalloc_tot + (long long)(D > 2 ? k + G : 0) * s->h.sz +
+                                    (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + G);
+                if (s->es == 4) {
+                    float f = (float)v;
+                    memcpy(&buf[o * 4], &f, 4);
+                } else {
+                    memcpy(&buf[o * 8], &v, 8);
+                }
+            }
+        }
+    });
     char* F = (char*)s->h.F;
     CU_CHECK(s, cudaMemcpyAsync(F + (size_t)comp_eb(ds.parity) * s->nalloc_tot * s->es, buf.data(), buf.size(),
                                 cudaMemcpyHostToDevice, st));
@@ -1221,34 +1239,38 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
                                     cudaMemcpyDeviceToHost, st));
         CU_CHECK(s, cudaStreamSynchronize(st));
         double* o = (double*)host_out;
-        for (int comp = 0; comp < 9; ++comp) {
-            const std::vector<char>& src = comp < 6 ? eb : jb;
-            const int sc = comp < 6 ? comp : comp - 6;
-            const int c = comp % 3;
-            for (int k = 0; k < ext[2]; ++k)
-                for (int j = 0; j < ext[1]; ++j)
-                    for (int i = 0; i < ext[0]; ++i) {
-                        const int g[3] = {i, j, k};
-                        bool has = true;
-                        for (int d = 0; d < D; ++d) {
-                            const bool stag = (comp < 3 || comp >= 6) ? (d == c) : (d != c);
-                            if (stag && g[d] > s->h.n[d] - 1) has = false;
-                        }
-                        double v = 0.0;
-                        if (has) {
-                            const long long idx = sc * s->nalloc_tot + (long long)(D > 2 ? k + G : 0) * s->h.sz +
-                                                  (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + G);
-                            if (es == 4) {
-                                float f;
-                                memcpy(&f, &src[idx * 4], 4);
-                                v = f;
-                            } else {
-                                memcpy(&v, &src[idx * 8], 8);
-                            }
-                        }
-                        o[comp * ne + ((long long)k * ext[1] + j) * ext[0] + i] = v;
+        // rows (comp, k, j) of the host array converted on up to 16 host threads
+        const long long nrows = 9LL * ext[2] * ext[1];
+        host_parallel(nrows, 256, [&](long long r0, long long r1) {
+            for (long long r = r0; r < r1; ++r) {
+                const int j = (int)(r % ext[1]), k = (int)((r / ext[1]) % ext[2]);
+                const int comp = (int)(r / ((long long)ext[1] * ext[2]));
+                const std::vector<char>& src = comp < 6 ? eb : jb;
+                const int sc = comp < 6 ? comp : comp - 6;
+                const int c = comp % 3;
+                for (int i = 0; i < ext[0]; ++i) {
+                    const int g[3] = {i, j, k};
+                    bool has = true;
+                    for (int d = 0; d < D; ++d) {
+                        const bool stag = (comp < 3 || comp >= 6) ? (d == c) : (d != c);
+                        if (stag && g[d] > s->h.n[d] - 1) has = false;
                     }
-        }
+                    double v = 0.0;
+                    if (has) {
+                        const long long idx = sc * s->nalloc_tot + (long long)(D > 2 ? k + G : 0) * s->h.sz +
+                                              (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + G);
+                        if (es == 4) {
+                            float f;
+                            memcpy(&f, &src[idx * 4], 4);
+                            v = f;
+                        } else {
+                            memcpy(&v, &src[idx * 8], 8);
+                        }
+                    }
+                    o[comp * ne + ((long long)k * ext[1] + j) * ext[0] + i] = v;
+                }
+            }
+        });
         return PIC_OK;
     }
     default:
@@ -1259,10 +1281,23 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
 pic_status pic_histogram(pic_sim* s, int n_e, double e_max, int n_a, double* host_out, void* stream)
 {
     if (!s || !host_out || n_e <= 0 || n_a <= 0 || !(e_max > 0)) return fail(s, PIC_EINVAL, "bad argument");
+    int prev = -1;
+    CU_CHECK(s, cudaGetDevice(&prev));
+    if (prev != s->device) CU_CHECK(s, cudaSetDevice(s->device));
+    struct Restore {
+        int d, now;
+        ~Restore()
+        {
+            if (d >= 0 && d != now) cudaSetDevice(d);
+        }
+    } restore{prev, s->device};
     cudaStream_t st = (cudaStream_t)stream;
     DevState ds;
     pic_status r = read_state(s, &ds, st);
     if (r != PIC_OK) return r;
+    if (ds.status & FLAG_TIMEOUT) return fail(s, PIC_ETIMEOUT, "a device wait timed out (status 0x%x)", ds.status);
+    if (ds.status & FLAG_CAPACITY)
+        return fail(s, PIC_ECAPACITY, "a particle found no slot in its destination tile (status 0x%x)", ds.status);
     const size_t nb = (size_t)n_e * n_a;
     if (nb > (size_t)s->nalloc_tot) return fail(s, PIC_ECAPACITY, "too many bins");
     CU_CHECK(s, cudaMemsetAsync(s->h.scratch, 0, nb * 8, st));

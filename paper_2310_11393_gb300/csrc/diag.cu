@@ -266,7 +266,7 @@ __global__ void k_eval_incident(const SimDev* __restrict__ sim, long long n, con
 }
 
 // ---- host wrappers ----
-static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 8)); }
+static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)device_sms() * 8)); }
 
 #define SFF_DISPATCH3(dim, prec, FN, ...)                       \
     do {                                                        \
@@ -362,6 +362,23 @@ std::mutex g_hist_mu;
 double* g_hist_addr[64] = {nullptr};   // device address of g_hist_bins per device ordinal
 }  // namespace
 
+namespace {
+// Makes `dev` the calling thread's current device for the guard's lifetime.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
 extern "C" pic_status pic_histogram_static(pic_sim* s, int n_e, double e_max, int n_a, double* host_out, void* stream)
 {
     if (!s || !host_out || n_e <= 0 || n_a <= 0 || !(e_max > 0)) return PIC_EINVAL;
@@ -369,9 +386,11 @@ extern "C" pic_status pic_histogram_static(pic_sim* s, int n_e, double e_max, in
         s->err = "pic_histogram_static: n_e * n_a exceeds PIC_HIST_STATIC_MAX_BINS (16384)";
         return PIC_EINVAL;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        s->err = "pic_histogram_static: no current CUDA device";
+    // the simulation's device is current for the look-up and every launch below
+    const int dev = s->device;
+    DeviceGuard guard(dev);
+    if (!guard.ok || dev < 0 || dev >= 64) {
+        s->err = "pic_histogram_static: cannot make the simulation's device current";
         return PIC_ENODEV;
     }
     double* bins = nullptr;
@@ -393,8 +412,21 @@ extern "C" pic_status pic_histogram_static(pic_sim* s, int n_e, double e_max, in
     sff::DevState ds;
     cudaError_t e = cudaMemcpyAsync(&ds, s->h.st, sizeof(sff::DevState), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        s->err = std::string("pic_histogram_static: ") + cudaGetErrorString(e);
+        return PIC_ECUDA;
+    }
+    // the device status word, as pic_diag reads it
+    if (ds.status & sff::FLAG_TIMEOUT) {
+        s->err = "pic_histogram_static: a device wait timed out";
+        return PIC_ETIMEOUT;
+    }
+    if (ds.status & sff::FLAG_CAPACITY) {
+        s->err = "pic_histogram_static: a particle found no slot in its destination tile";
+        return PIC_ECAPACITY;
+    }
     const size_t nb = (size_t)n_e * n_a;
-    if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, nb * sizeof(double), st);
+    e = cudaMemsetAsync(bins, 0, nb * sizeof(double), st);
     if (e == cudaSuccess) {
         sff::launch_histogram(s->d, s->cfg.dim, s->cfg.precision, s->h.cap,
                               std::min<long long>(ds.n_exits, s->h.max_exits), n_e, e_max, n_a, bins, st);

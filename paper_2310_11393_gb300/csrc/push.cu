@@ -906,17 +906,20 @@ __global__ void __launch_bounds__(1024) k_scan_lb(const SimDev* __restrict__ sim
         unsigned long long* fl = S.scanflags;
         const unsigned long long agg = ((unsigned long long)s_tk << 31) | (unsigned long long)s_tc;
         long long pk = 0, pc = 0;
+        // a held block (test aid) publishes nothing: the blocks after it wait out their bound
+        const bool publish = b != S.scan_hold;
         if (b == 0) {
-            atomicExch(&fl[0], (2ull << 62) | agg);
+            if (publish) atomicExch(&fl[0], (2ull << 62) | agg);
         } else {
-            atomicExch(&fl[b], (1ull << 62) | agg);
+            if (publish) atomicExch(&fl[b], (1ull << 62) | agg);
             bool ok = true;
+            const int limit = S.scan_spins;
             for (int j = b - 1; j >= 0; --j) {
                 unsigned long long f = 0;
                 int spins = 0;
                 do {
                     f = *reinterpret_cast<volatile unsigned long long*>(&fl[j]);
-                } while ((f >> 62) == 0 && ++spins < (1 << 22));
+                } while ((f >> 62) == 0 && ++spins < limit);
                 if ((f >> 62) == 0) {
                     ok = false;
                     break;
@@ -929,8 +932,9 @@ __global__ void __launch_bounds__(1024) k_scan_lb(const SimDev* __restrict__ sim
                 atomicOr(&S.st->status, (unsigned)FLAG_TIMEOUT);
                 pk = pc = 0;
             }
-            atomicExch(&fl[b], (2ull << 62) | ((unsigned long long)(pk + s_tk) << 31) |
-                                   (unsigned long long)(pc + s_tc));
+            if (publish)
+                atomicExch(&fl[b], (2ull << 62) | ((unsigned long long)(pk + s_tk) << 31) |
+                                       (unsigned long long)(pc + s_tc));
         }
         s_pk = (int)pk;
         s_pc = (int)pc;
@@ -1411,7 +1415,7 @@ void launch_scan_one(const SimDev* sim, int q, cudaStream_t s) { k_scan_one<<<1,
 template <int D, typename R>
 static void frame_t(const SimDev* sim, int q, long long n, cudaStream_t s)
 {
-    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)device_sms() * 16));
     if (n > 0) k_frame_linear<D><<<grid, 256, 0, s>>>(sim, q, n);
     k_next_slots<<<1, 1024, 0, s>>>(sim, q);
 }
@@ -1424,7 +1428,7 @@ template <int D, typename R>
 static void gen_t(const SimDev* sim, long long n, int ppc, const int lo[3], const int sn[3], unsigned long long seed,
                   double w, cudaStream_t s)
 {
-    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    const int grid = (int)std::min<long long>((n + 255) / 256, (long long)device_sms() * 16);
     if (n > 0) k_gen_slab<D, R><<<grid, 256, 0, s>>>(sim, n, ppc, lo[0], lo[1], lo[2], sn[0], sn[1], seed, w);
 }
 void launch_gen_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int slab_lo[3],
@@ -1436,7 +1440,7 @@ void launch_gen_slab(const SimDev* sim, int dim, int prec, long long n, int ppc,
 template <int D, typename R>
 static void count_t(const SimDev* sim, long long n, cudaStream_t s)
 {
-    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    const int grid = (int)std::min<long long>((n + 255) / 256, (long long)device_sms() * 16);
     if (n > 0) k_count_linear<D><<<grid, 256, 0, s>>>(sim, n);
 }
 void launch_count_linear(const SimDev* sim, int dim, int prec, long long n, cudaStream_t s)
@@ -1447,13 +1451,13 @@ void launch_count_linear(const SimDev* sim, int dim, int prec, long long n, cuda
 template <int D, typename R>
 static void sortlin_t(const SimDev* sim, long long n, cudaStream_t s)
 {
-    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    const int grid = (int)std::min<long long>((n + 255) / 256, (long long)device_sms() * 16);
     if (n > 0) k_sort_linear<D, R><<<grid, 256, 0, s>>>(sim, n);
 }
 template <int D, typename R>
 static void place_t(const SimDev* sim, long long n, int ppc, const int lo[3], const int hi[3], cudaStream_t s)
 {
-    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    const int grid = (int)std::min<long long>((n + 255) / 256, (long long)device_sms() * 16);
     if (n > 0) k_place_slab<D, R><<<grid, 256, 0, s>>>(sim, n, ppc, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
 }
 void launch_place_slab(const SimDev* sim, int dim, int prec, long long n, int ppc, const int lo[3], const int hi[3],

@@ -118,6 +118,8 @@ struct alignas(128) SimDev {
     unsigned long long* scanflags;   // multi-block tile scan: per block status | particles | chunks
     int* scanticket;          // multi-block tile scan: block order ticket
     int nscanblk;             // blocks of the multi-block tile scan (tiles / 4096, rounded up)
+    int scan_spins;           // polls of a predecessor's flag before the look-back gives up
+    int scan_hold;            // test aid: this scan block publishes nothing (-1: none)
     double* exits;            // [max_exits][EXIT_DOUBLES]
     long long max_exits;
     long long cap;            // slots per buffer set (frame factor x particle capacity)

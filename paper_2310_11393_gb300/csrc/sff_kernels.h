@@ -88,6 +88,9 @@ void launch_histogram(const SimDev* sim, int dim, int prec, long long n_alive, l
 void launch_eval_incident(const SimDev* sim, int dim, int prec, long long n, const double* pts, double* out,
                           cudaStream_t s);
 
+// streaming multiprocessors of the current device (queried once per device)
+int device_sms();
+
 // kernel attributes (dynamic shared memory opt-in); returns blocks per SM
 int prepare_push(int dim, int prec, size_t smem);
 int prepare_yee(int dim, int prec, size_t smem);

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pic.h"
+#include "sff_kernels.h"
 
 namespace {
 
@@ -161,7 +162,7 @@ extern "C" pic_status pic_autotune(pic_config* cfg, int trial_steps, void* strea
             long long vol = 1;
             for (int d = 0; d < cfg->dim; ++d) vol *= t[d];
             // (unless the particles are too few to give every SM several work items anyway)
-            if (k > 0 && cfg->ppc > 0 && vol * cfg->ppc < 2048 && p.n_particles / 2048 > 4 * 152) continue;
+            if (k > 0 && cfg->ppc > 0 && vol * cfg->ppc < 2048 && p.n_particles / 2048 > 4LL * sff::device_sms()) continue;
             pic_config cand = c;
             for (int d = 0; d < 3; ++d) cand.tile[d] = d < cfg->dim ? t[d] : 0;
             if (tune_chunk) cand.chunk = 0;

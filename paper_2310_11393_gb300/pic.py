@@ -69,6 +69,11 @@ class pic_result(Structure):
                 ("pushes", c_int64)]
 
 
+class pic_peaks(Structure):
+    _fields_ = [("sms", c_int32), ("fp32_tflops", c_double), ("fp64_tflops", c_double), ("sfu_gops", c_double),
+                ("sm_clock_mhz", c_double), ("fp32_flop_per_clk_sm", c_double)]
+
+
 _lib = None
 
 
@@ -129,6 +134,10 @@ def load():
     L.pic_serve_clock.argtypes = [P]
     L.pic_serve_close.restype = c_int
     L.pic_serve_close.argtypes = [P]
+    L.pic_test_hold_scan.restype = c_int
+    L.pic_test_hold_scan.argtypes = [P, c_int, c_int]
+    L.pic_probe_peaks.restype = c_int
+    L.pic_probe_peaks.argtypes = [POINTER(pic_peaks), P]
     _lib = L
     return L
 
@@ -244,6 +253,18 @@ def pic_autotune(cfg: pic_config, trial_steps: int = 4, stream=0) -> float:
     ms = c_double()
     check(load().pic_autotune(byref(cfg), int(trial_steps), c_void_p(stream), byref(ms)))
     return ms.value
+
+
+def pic_test_hold_scan(sim, block: int, spins: int):
+    """Test aid: one tile-scan block stops publishing, so the look-back waits after it time out."""
+    return check(load().pic_test_hold_scan(sim, int(block), int(spins)), sim)
+
+
+def pic_probe_peaks(stream=0) -> pic_peaks:
+    """Measured FP32 / FP64 / special-function issue rates and SM clock of the current device."""
+    out = pic_peaks()
+    check(load().pic_probe_peaks(byref(out), c_void_p(stream)))
+    return out
 
 
 def pic_batch_step(sims, n_steps: int, stream=0):

@@ -10,7 +10,7 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-STRUCTS = ["pic_config", "pic_params", "pic_info", "pic_allocator", "pic_serve_config", "pic_result"]
+STRUCTS = ["pic_config", "pic_params", "pic_info", "pic_allocator", "pic_serve_config", "pic_result", "pic_peaks"]
 
 
 @pytest.fixture(scope="module")

@@ -1,11 +1,10 @@
 """CUDA path (through the C-ABI) against the FP64 oracle on the same seeded inputs.
 
 Tolerances (the spec bar, made concrete):
-  * FP32 runs, first 50 steps: per particle |p_gpu - p_ref| / max(|p_ref|, a0) <= 1e-5, a0 being
-    the quiver-momentum scale (single precision evaluates the incident field to ~5e-7 of its
-    amplitude; impulses of size ~a0 dt add up and cancel over a cycle, so |p_gpu - p_ref| grows
-    like N dt C u a0 ~ 4e-6 a0 after 50 steps with u = 6e-8 and C ~ 10, while |p| itself can
-    be arbitrarily small);
+  * FP32 runs, first 50 steps: per particle |p_gpu - p_ref| / max(|p_ref|, 1e-2 a0) <= 1e-5,
+    a0 being the quiver-momentum scale (single precision evaluates the incident field to
+    ~5e-7 of its amplitude; impulses of size ~a0 dt add up and cancel over a cycle, so
+    |p_gpu - p_ref| is set by the field amplitude while |p| itself can pass through zero);
     per field component max|F_gpu - F_ref| / max|F_ref| <= 1e-5;
   * FP64 runs: the same quantities to 1e-9 (only the summation order of deposits differs);
   * integer and index data (particle ids, which particles left the box, cell indices after
@@ -139,24 +138,25 @@ def test_2d_lp_parity_first_50_steps(P, orc, prec):
         assert err < tol, (step, err)
     assert max(np.abs(pr["u"]).max() for _, _, pr in hist) > 1.0          # relativistic by step 50
     fe = field_errors(sim.fields(), ref.fields())
-    assert fe[:6].max() < tol, fe
-    assert fe[6:].max() < 10 * tol, fe
+    print(f"2D LP {prec}: momentum {err:.2e}, E/B {fe[:6].max():.2e}, J {fe[6:].max():.2e}")
+    assert fe.max() < tol, fe
     e_g, e_r = sim.energies(), ref.energies()
-    assert abs(e_g[0] / e_r[0] - 1) < 10 * tol
-    assert abs(e_g[2] / e_r[2] - 1) < 10 * tol
+    assert abs(e_g[0] / e_r[0] - 1) < tol
+    assert abs(e_g[2] / e_r[2] - 1) < tol
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_3d_rp_parity(P, orc, prec):
-    w = small_3d(precision=synth.FP32 if prec == "fp32" else synth.FP64)
-    sim, ref, hist = run_pair(P, orc, w, 30, check_every=10)
+def test_3d_rp_parity_first_50_steps(P, orc, prec):
+    w = small_3d(precision=synth.FP32 if prec == "fp32" else synth.FP64, steps=50)
+    sim, ref, hist = run_pair(P, orc, w, 50, check_every=10)
     tol = 1e-5 if prec == "fp32" else 1e-9
     for step, pg, pr in hist:
         err, n = momentum_error(pg, pr, w.a0)
         assert set(pg["id"].tolist()) == set(pr["id"].tolist()), step
         assert err < tol, (step, err)
     fe = field_errors(sim.fields(), ref.fields())
-    assert fe[:6].max() < tol, fe
+    print(f"3D RP {prec}: momentum {err:.2e}, E/B {fe[:6].max():.2e}, J {fe[6:].max():.2e}")
+    assert fe.max() < tol, fe
 
 
 def test_gauss_law_on_the_gpu(P):
@@ -211,7 +211,7 @@ def test_full_size_first_push_on_sampled_particles(P, orc, wl):
     pr = ref.particles()
     err, n = momentum_error(pg, pr, w.a0)
     assert n == len(pr["id"])
-    assert err < 1e-6, err
+    assert err < 1e-5, err
     assert position_error(pg, pr, w.dx) < 1e-5
 
 
