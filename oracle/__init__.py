@@ -94,6 +94,8 @@ def lib():
             L.orc_create.argtypes = [ctypes.POINTER(OrcConfig)]
             L.orc_destroy.argtypes = [ctypes.c_void_p]
             L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_step_particles.argtypes = [ctypes.c_void_p]
+            L.orc_step_fields.argtypes = [ctypes.c_void_p]
             for f in ("orc_num_particles", "orc_num_exits", "orc_step_index"):
                 getattr(L, f).restype = ctypes.c_int64
                 getattr(L, f).argtypes = [ctypes.c_void_p]
@@ -163,6 +165,14 @@ class Sim:
 
     def step(self, n: int = 1):
         self._L.orc_step(self.h, int(n))
+
+    def step_particles(self):
+        """First part of one step: gather, incident field, push, move, deposit, exits."""
+        self._L.orc_step_particles(self.h)
+
+    def step_fields(self):
+        """Second part of one step: Yee update driven by the deposited J, step counter."""
+        self._L.orc_step_fields(self.h)
 
     @property
     def step_index(self) -> int:

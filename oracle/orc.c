@@ -934,69 +934,84 @@ static void incident_on_nodes(orc_sim* s, double t)
                 }
 }
 
-void orc_step(orc_sim* s, int nsteps)
+/* First part of a step (Sec. 2 cycle): J cleared, then for every electron the gather, the
+ * incident field at its position, the momentum update, the move and its Esirkepov current;
+ * electrons that leave are recorded as exits. */
+void orc_step_particles(orc_sim* s)
 {
     const double dt = s->c.dt, dx = s->c.dx;
     const double q = -1.0;
-    for (int it = 0; it < nsteps; it++) {
-        double t = s->step * dt;
-        int64_t keep = 0;
-        /* J of this step; it stays readable after the step as J^{n+1/2} */
-        for (int c = 6; c < 9; c++) memset(s->F[c], 0, sizeof(double) * s->nnode);
-        const int inc_grid = s->c.incident_grid && s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode;
-        if (inc_grid) incident_on_nodes(s, t);
-        for (int64_t p = 0; p < s->np; p++) {
-            double* x = &s->px[3 * p];
-            double* u = &s->pu[3 * p];
-            double X[3] = {x[0] / dx, x[1] / dx, x[2] / dx};
-            double E[3], B[3];
-            for (int c = 0; c < 3; c++) { E[c] = gather(s, c, X); B[c] = gather(s, 3 + c, X); }
-            if (inc_grid) {
-                for (int c = 0; c < 3; c++) {
-                    E[c] += gather_from(s, s->Finc[c], c, X);
-                    B[c] += gather_from(s, s->Finc[3 + c], 3 + c, X);
-                }
-            } else if (s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode) {
-                double Ei[3], Bi[3];
-                orc_incident(&s->c, x, t, Ei, Bi);
-                for (int c = 0; c < 3; c++) { E[c] += Ei[c]; B[c] += Bi[c]; }
+    double t = s->step * dt;
+    int64_t keep = 0;
+    /* J of this step; it stays readable after the step as J^{n+1/2} */
+    for (int c = 6; c < 9; c++) memset(s->F[c], 0, sizeof(double) * s->nnode);
+    const int inc_grid = s->c.incident_grid && s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode;
+    if (inc_grid) incident_on_nodes(s, t);
+    for (int64_t p = 0; p < s->np; p++) {
+        double* x = &s->px[3 * p];
+        double* u = &s->pu[3 * p];
+        double X[3] = {x[0] / dx, x[1] / dx, x[2] / dx};
+        double E[3], B[3];
+        for (int c = 0; c < 3; c++) { E[c] = gather(s, c, X); B[c] = gather(s, 3 + c, X); }
+        if (inc_grid) {
+            for (int c = 0; c < 3; c++) {
+                E[c] += gather_from(s, s->Finc[c], c, X);
+                B[c] += gather_from(s, s->Finc[3 + c], 3 + c, X);
             }
-            /* momentum update of the Lorentz force (charge q, mass 1) */
-            const double h = 0.5 * q * dt;
-            if (s->c.pusher == ORC_PUSHER_VAY) push_vay(u, E, B, h);
-            else if (s->c.pusher == ORC_PUSHER_HC) push_higuera_cary(u, E, B, h);
-            else push_boris(u, E, B, h);
-            double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            double v[3] = {u[0] / g, u[1] / g, u[2] / g};
-            double xn[3] = {x[0], x[1], x[2]};
-            for (int d = 0; d < s->c.dim; d++) xn[d] = x[d] + dt * v[d];
-            deposit(s, x, xn, v, s->pw[p]);
-            int out = 0;
-            for (int d = 0; d < s->c.dim; d++) {
-                if (periodic(s)) {
-                    double L = s->c.n[d] * dx;
-                    xn[d] = fmod(xn[d], L);
-                    if (xn[d] < 0) xn[d] += L;
-                } else {
-                    double Xn = xn[d] / dx;
-                    if (Xn < s->c.remove_margin || Xn >= s->c.n[d] - s->c.remove_margin) out = 1;
-                }
-            }
-            if (out) {
-                add_exit(s, u, s->pw[p], s->pid[p]);
-                continue;
-            }
-            for (int d = 0; d < 3; d++) {
-                s->px[3 * keep + d] = xn[d];
-                s->pu[3 * keep + d] = u[d];
-            }
-            s->pw[keep] = s->pw[p];
-            s->pid[keep] = s->pid[p];
-            keep++;
+        } else if (s->c.beam != ORC_BEAM_NONE && !s->c.tf_mode) {
+            double Ei[3], Bi[3];
+            orc_incident(&s->c, x, t, Ei, Bi);
+            for (int c = 0; c < 3; c++) { E[c] += Ei[c]; B[c] += Bi[c]; }
         }
-        s->np = keep;
-        yee(s);
-        s->step++;
+        /* momentum update of the Lorentz force (charge q, mass 1) */
+        const double h = 0.5 * q * dt;
+        if (s->c.pusher == ORC_PUSHER_VAY) push_vay(u, E, B, h);
+        else if (s->c.pusher == ORC_PUSHER_HC) push_higuera_cary(u, E, B, h);
+        else push_boris(u, E, B, h);
+        double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        double v[3] = {u[0] / g, u[1] / g, u[2] / g};
+        double xn[3] = {x[0], x[1], x[2]};
+        for (int d = 0; d < s->c.dim; d++) xn[d] = x[d] + dt * v[d];
+        deposit(s, x, xn, v, s->pw[p]);
+        int out = 0;
+        for (int d = 0; d < s->c.dim; d++) {
+            if (periodic(s)) {
+                double L = s->c.n[d] * dx;
+                xn[d] = fmod(xn[d], L);
+                if (xn[d] < 0) xn[d] += L;
+            } else {
+                double Xn = xn[d] / dx;
+                if (Xn < s->c.remove_margin || Xn >= s->c.n[d] - s->c.remove_margin) out = 1;
+            }
+        }
+        if (out) {
+            add_exit(s, u, s->pw[p], s->pid[p]);
+            continue;
+        }
+        for (int d = 0; d < 3; d++) {
+            s->px[3 * keep + d] = xn[d];
+            s->pu[3 * keep + d] = u[d];
+        }
+        s->pw[keep] = s->pw[p];
+        s->pid[keep] = s->pid[p];
+        keep++;
+    }
+    s->np = keep;
+}
+
+/* Second part of a step: the Yee update of the scattered field driven by that J, then the
+ * step counter. */
+void orc_step_fields(orc_sim* s)
+{
+    yee(s);
+    s->step++;
+}
+
+void orc_step(orc_sim* s, int nsteps)
+{
+    for (int it = 0; it < nsteps; it++) {
+        orc_step_particles(s);
+        orc_step_fields(s);
     }
 }
 

@@ -73,6 +73,10 @@ typedef struct orc_sim orc_sim;
 orc_sim* orc_create(const orc_config* cfg);          /* seeded slab particles (may be none), zero scattered field */
 void     orc_destroy(orc_sim* s);
 void     orc_step(orc_sim* s, int nsteps);
+/* the two parts of one step (orc_step runs them in turn): particles (J cleared, gather,
+ * incident field, push, move, deposit, exits), then fields (Yee update, step counter) */
+void     orc_step_particles(orc_sim* s);
+void     orc_step_fields(orc_sim* s);
 int64_t  orc_num_particles(const orc_sim* s);          /* alive */
 int64_t  orc_num_exits(const orc_sim* s);
 int64_t  orc_step_index(const orc_sim* s);
