@@ -165,8 +165,10 @@ typedef struct {
 } pic_info;
 
 /* Device memory provider.  alloc(bytes, ctx) returns device memory (256-byte aligned)
- * or NULL; free(ptr, ctx) releases it.  Both are called only from pic_init and
- * pic_destroy on the calling thread.  A NULL pic_allocator* means cudaMalloc/cudaFree. */
+ * or NULL; free(ptr, ctx) releases it.  Both are called only on the calling thread, from
+ * pic_init and pic_destroy, and from pic_batch_step for the launch tables of a new list of
+ * simulations (taken from its first member's provider and given back when any member is
+ * destroyed).  A NULL pic_allocator* means cudaMalloc/cudaFree. */
 typedef struct {
     void* (*alloc)(size_t bytes, void* ctx);
     void (*free)(void* ptr, void* ctx);

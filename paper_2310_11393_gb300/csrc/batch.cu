@@ -20,6 +20,11 @@ namespace {
 struct GroupRes {
     Group g{};
     void* mem = nullptr;
+    // the group tables come from the first member's device-memory provider (pic_allocator, or
+    // cudaMalloc when it gave none) and go back to it; an entry is dropped (batch_forget) when
+    // any member is destroyed, before that member releases anything
+    pic_allocator al{};
+    bool cuda = true;
 };
 
 struct BatchEntry {
@@ -50,8 +55,11 @@ void free_entry(BatchEntry* e)
     if (e->cs2) cudaStreamDestroy(e->cs2);
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
     if (e->ev_join) cudaEventDestroy(e->ev_join);
-    for (auto& gr : e->groups)
-        if (gr.mem) cudaFree(gr.mem);
+    for (auto& gr : e->groups) {
+        if (!gr.mem) continue;
+        if (gr.cuda) cudaFree(gr.mem);
+        else gr.al.free(gr.mem, gr.al.ctx);
+    }
     delete e;
 }
 
@@ -80,7 +88,15 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         }
         const size_t bytes = a256(sizeof(SimDev) * n) + a256(sizeof(Work) * nyw) + a256(sizeof(int) * (n + 1)) + a256(64);
         GroupRes gr;
-        if (cudaMalloc(&gr.mem, bytes) != cudaSuccess) {
+        const pic_sim* owner = sims[mem[0]];
+        gr.cuda = owner->use_cuda_malloc;
+        gr.al = owner->alloc;
+        if (gr.cuda) {
+            if (cudaMalloc(&gr.mem, bytes) != cudaSuccess) gr.mem = nullptr;
+        } else {
+            gr.mem = gr.al.alloc(bytes, gr.al.ctx);
+        }
+        if (!gr.mem) {
             err = "batch descriptor allocation failed";
             free_entry(e);
             return PIC_ENOMEM;
@@ -107,6 +123,7 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         cudaMemset(d_cnt, 0, 64);
         Group& g = gr.g;
         g.sims = d_sims;
+        g.one = nullptr;
         g.nsims = n;
         g.gprefix = d_gp;
         g.ywork = d_yw;

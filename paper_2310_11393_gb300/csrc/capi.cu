@@ -777,6 +777,8 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     INIT_CHECK(cudaMemsetAsync(h.rho_ion, 0, (size_t)L.natot * 8, st));
     DevState ds{};
     ds.parity = 1;
+    // the slab's weights are n_e f(x)/ppc with f <= 1 (rounded up: every FP32 weight is below)
+    ds.wmax = cfg->ppc > 0 ? std::nextafter((float)(cfg->n_e / cfg->ppc), INFINITY) : 0.f;
     INIT_CHECK(cudaMemcpyAsync(h.st, &ds, sizeof ds, cudaMemcpyHostToDevice, st));
     INIT_CHECK(cudaMemcpyAsync(s->d, &h, sizeof h, cudaMemcpyHostToDevice, st));
     // work lists of the single-simulation group
@@ -816,6 +818,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     const int nsm = prop.multiProcessorCount;
     Group& g = s->grp;
     g.sims = s->d;
+    g.one = &s->h;       // the same descriptor, by value for the push (final from here on)
     g.gprefix = s->d_gprefix;
     g.ywork = s->d_ywork;
     g.nywork = L.nytiles;
@@ -1056,6 +1059,13 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
     // fields live in the set matching parity 0 now; keep the present field values
     DevState ds;
     if ((r = read_state(s, &ds, st)) != PIC_OK) return r;
+    {
+        // largest |weight| (rounded up in FP32): the scale of the FP32 push's fixed-point current
+        double wm = 0.0;
+        for (long long p = 0; p < n; ++p) wm = std::max(wm, std::fabs(w[p]));
+        ds.wmax = wm > 0 ? std::nextafter((float)wm, INFINITY) : 0.f;
+        if ((r = write_state(s, ds, st)) != PIC_OK) return r;
+    }
     if (ds.step == 0) return compute_rho_ion(s, st);
     return PIC_OK;
 }

@@ -92,14 +92,24 @@ __device__ __forceinline__ R interp(const R* f, int bx, int bxy, const int b0, c
     }
 }
 
-__device__ __forceinline__ void sm_add(float* a, float v)
+// Current accumulation in the work item's shared-memory box.  FP32: 32-bit fixed point with
+// the scale q = 2^30 / (N w_max) of the item (N particles): a contribution of one particle to
+// one node is bounded by w |v| <= w_max (Esirkepov's partial sums of the shape change are at
+// most the move in cells, v dt/dx, times dx/dt; the transverse weights are averages of shapes
+// in [0, 1]; |v| < c = 1), so no node's sum can leave the 32-bit range.  A shared-memory
+// integer add is one native reduction, where the FP32 add is a compare-and-swap loop with a
+// round trip per attempt.  The box is turned back into FP32 before its TMA reduce-add; the
+// rounding of each contribution to 1/q is below 2^-30 N w_max.  FP64 keeps double sums.
+__device__ __forceinline__ void jdep(float* a, float v, float q)
 {
-    if (v != 0.0f) atomicAdd(a, v);
+    const int iv = __float2int_rn(v * q);
+    if (iv != 0) atomicAdd(reinterpret_cast<int*>(a), iv);
 }
-__device__ __forceinline__ void sm_add(double* a, double v)
+__device__ __forceinline__ void jdep(double* a, double v, double)
 {
     if (v != 0.0) atomicAdd(a, v);
 }
+constexpr float JQ_RANGE = 1073741824.0f;   // 2^30
 
 // Global chunk k of a launch group -> simulation, tile and particle slots.  Chunks are
 // numbered per simulation by the tile scan (ctile / crange) and across the group by gprefix.
@@ -246,13 +256,44 @@ __device__ __forceinline__ void frame_count(const SimDev& S, const int cn[3], co
     }
 }
 
+// Threads of a push block and blocks per SM the registers are budgeted for.  The 3D FP32
+// push shares its 101 KB box (16x8x4 tiles) among 512 threads at 64 registers: two blocks
+// keep 32 warps per SM busy instead of 16 with 256-thread blocks at 128 registers.
+template <int D, typename R>
+__host__ __device__ constexpr int push_threads()
+{
+    return (D == 3 && sizeof(R) == 4) ? 512 : 256;
+}
+template <int D, typename R>
+__host__ __device__ constexpr int push_min_blocks()
+{
+    return sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2);
+}
+
+// Chunk k of a single simulation (its chunks are numbered from gprefix[0]).
+__device__ __forceinline__ ChunkRef chunk_of_one(const SimDev& S, const int* __restrict__ gprefix, int k)
+{
+    const int par = S.st->parity;
+    const int j = k - gprefix[0];
+    const int2 pr = S.crange[par][j];
+    ChunkRef r;
+    r.sim = 0;
+    r.tile = S.ctile[par][j];
+    r.p0 = pr.x;
+    r.p1 = pr.y;
+    return r;
+}
+
+// The push of a launch group (see k_push / k_push1 below).  ONE: the group is one simulation
+// whose descriptor `one` is a kernel parameter (constant bank: its fields cost no load
+// instruction, and the tensor maps are used from parameter space); otherwise the
+// descriptors of the group's simulations are read from the device array `sims`.
 // `sorting`: this step's re-sort orders the tiles by cell; then the simulations that have a
 // cell sort are pushed in place (k_scatter places them) and the others straight into the
 // other buffer set like every step.
-template <int D, typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_push(const SimDev* __restrict__ sims, int nsims,
-                                              const int* __restrict__ gprefix, int* __restrict__ counter,
-                                              int sorting)
+template <int D, typename R, bool ONE>
+__device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const SimDev& one, int nsims,
+                                          const int* __restrict__ gprefix, int* __restrict__ counter, int sorting)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -275,8 +316,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         const int item = s_item;
         __syncthreads();
         if (item >= gprefix[nsims]) break;
-        const ChunkRef ck = chunk_of(sims, nsims, gprefix, item);
-        const SimDev& S = sims[ck.sim];
+        const ChunkRef ck = ONE ? chunk_of_one(one, gprefix, item) : chunk_of(sims, nsims, gprefix, item);
+        const SimDev& S = ONE ? one : sims[ck.sim];
         DevState* st = S.st;
         const int par = st->parity, np = 1 - par;
         const int p0 = ck.p0, p1 = ck.p1;
@@ -303,7 +344,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         if (tid == 0) {
             // the maps were written to device memory before the launch: one acquire per
             // simulation and block orders that write before this thread's TMA uses
-            if (ck.sim != acq_sim) {
+            if (!ONE && ck.sim != acq_sim) {
                 tensormap_acquire(&S.tm_pf);
                 tensormap_acquire(&S.tm_pj);
                 acq_sim = ck.sim;
@@ -329,12 +370,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
 
         const BeamC<R>& bc = beam_of<R>(S);
         const PhaseRef<R> pref = s_pref;
+        // fixed-point scale of this item's current (FP32; unused in FP64)
+        const float wmax = st->wmax;
+        const R jq = (sizeof(R) == 4 && wmax > 0.f) ? R(JQ_RANGE / ((float)(p1 - p0) * wmax)) : R(0);
         const R dtdx = bc.dtdx;
         const R jfac = bc.jfac;                     // -q dx/dt, q = -1
         const R hq = bc.hq;                         // q dt / 2
         const int hx[3] = {4, 2, 2};                // box halo below the tile per axis
 
-        // Rounds of 256 particles.  With P particles per cell (1, 2, 4 or 8) sitting next to
+        // Rounds of nth particles (256 or 512).  With P particles per cell (1, 2, 4 or 8) sitting next to
         // each other after the sort, lane l of warp w takes particle P l + (w mod P) of the
         // round's (w div P)-th group of 32 P: the 32 lanes of a warp then sit in 32
         // consecutive cells, so the same stencil node of the deposit and the gather is a
@@ -464,14 +508,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                     for (int a = 0; a < 3; ++a) {
                         if (a >= nw[0] - 1) break;
                         acc += cw * DS[0][a];
-                        sm_add(&Jx[jw[0] + a], acc);
+                        jdep(&Jx[jw[0] + a], acc, jq);
                     }
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         if (a >= nw[0]) break;
                         const R f = S0[0][a] + R(0.5) * DS[0][a];
-                        sm_add(&Jy[jw[0] + a], -wt * v[1] * f);
-                        sm_add(&Jz[jw[0] + a], -wt * v[2] * f);
+                        jdep(&Jy[jw[0] + a], -wt * v[1] * f, jq);
+                        jdep(&Jz[jw[0] + a], -wt * v[2] * f, jq);
                     }
                 } else if constexpr (D == 2) {
 #pragma unroll
@@ -483,7 +527,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                         for (int a = 0; a < 3; ++a) {
                             if (a >= nw[0] - 1) break;
                             acc += cw * DS[0][a] * fy;
-                            sm_add(&Jx[(jw[1] + b) * bx + jw[0] + a], acc);
+                            jdep(&Jx[(jw[1] + b) * bx + jw[0] + a], acc, jq);
                         }
                     }
 #pragma unroll
@@ -495,7 +539,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                         for (int b = 0; b < 3; ++b) {
                             if (b >= nw[1] - 1) break;
                             acc += cw * DS[1][b] * fx;
-                            sm_add(&Jy[(jw[1] + b) * bx + jw[0] + a], acc);
+                            jdep(&Jy[(jw[1] + b) * bx + jw[0] + a], acc, jq);
                         }
                     }
                     const R qv = -wt * v[2];
@@ -507,7 +551,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                             if (a >= nw[0]) break;
                             const R wz = S0[0][a] * S0[1][b] + R(0.5) * DS[0][a] * S0[1][b] +
                                          R(0.5) * S0[0][a] * DS[1][b] + third * DS[0][a] * DS[1][b];
-                            sm_add(&Jz[(jw[1] + b) * bx + jw[0] + a], qv * wz);
+                            jdep(&Jz[(jw[1] + b) * bx + jw[0] + a], qv * wz, jq);
                         }
                     }
                 } else {
@@ -524,7 +568,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                             for (int a = 0; a < 3; ++a) {
                                 if (a >= nw[0] - 1) break;
                                 acc += cw * DS[0][a] * fyz;
-                                sm_add(&Jx[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                                jdep(&Jx[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc, jq);
                             }
                         }
                     }
@@ -541,7 +585,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                             for (int b = 0; b < 3; ++b) {
                                 if (b >= nw[1] - 1) break;
                                 acc += cw * DS[1][b] * fxz;
-                                sm_add(&Jy[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                                jdep(&Jy[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc, jq);
                             }
                         }
                     }
@@ -558,7 +602,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
                             for (int cc = 0; cc < 3; ++cc) {
                                 if (cc >= nw[2] - 1) break;
                                 acc += cw * DS[2][cc] * fxy;
-                                sm_add(&Jz[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc);
+                                jdep(&Jz[(jw[2] + cc) * bxy + (jw[1] + b) * bx + jw[0] + a], acc, jq);
                             }
                         }
                     }
@@ -644,6 +688,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
 
         // ---- current flush and destination-tile counts ----
         if constexpr (sizeof(R) == 4) {
+            // fixed point back to FP32, in place
+            const float inv = (float)(p1 - p0) * wmax * (1.0f / JQ_RANGE);
+            int* Jq = reinterpret_cast<int*>(Js);
+            for (int i = tid; i < 3 * bvol; i += nth) Jq[i] = __float_as_int(__int2float_rn(Jq[i]) * inv);
+            __syncthreads();
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -697,6 +746,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (D <= 2 ? 4 : 2)) k_
         __syncthreads();
     }
     if (tid == 0) bulk_wait0();
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(push_threads<D, R>(), push_min_blocks<D, R>())
+    k_push(const SimDev* __restrict__ sims, int nsims, const int* __restrict__ gprefix, int* __restrict__ counter,
+           int sorting)
+{
+    push_body<D, R, false>(sims, *sims, nsims, gprefix, counter, sorting);
+}
+
+// one simulation: the descriptor by value in the kernel's parameters
+template <int D, typename R>
+__global__ void __launch_bounds__(push_threads<D, R>(), push_min_blocks<D, R>())
+    k_push1(const __grid_constant__ SimDev one, const int* __restrict__ gprefix, int* __restrict__ counter, int sorting)
+{
+    push_body<D, R, true>(nullptr, one, 1, gprefix, counter, sorting);
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim a multiple of 32, <= 1024).
@@ -1353,7 +1418,12 @@ __global__ void k_place_slab(const SimDev* __restrict__ sim, long long n, int pp
 template <int D, typename R>
 static void push_t(const Group& g, bool sorting, cudaStream_t s)
 {
-    k_push<D, R><<<g.push_grid, 256, g.push_smem, s>>>(g.sims, g.nsims, g.gprefix, g.counters + 0, sorting ? 1 : 0);
+    if (g.one)
+        k_push1<D, R><<<g.push_grid, push_threads<D, R>(), g.push_smem, s>>>(*g.one, g.gprefix, g.counters + 0,
+                                                                              sorting ? 1 : 0);
+    else
+        k_push<D, R><<<g.push_grid, push_threads<D, R>(), g.push_smem, s>>>(g.sims, g.nsims, g.gprefix,
+                                                                             g.counters + 0, sorting ? 1 : 0);
 }
 template <int D, typename R>
 static void cellsort_t(const Group& g, cudaStream_t s)
@@ -1475,7 +1545,11 @@ template <int D, typename R>
 static void attr_push(size_t smem, int* out)
 {
     cudaFuncSetAttribute(k_push<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_push<D, R>, 256, smem);
+    cudaFuncSetAttribute(k_push1<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push<D, R>, push_threads<D, R>(), smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push1<D, R>, push_threads<D, R>(), smem);
+    *out = std::min(a, b);
 }
 int prepare_push(int dim, int prec, size_t smem)
 {

@@ -28,7 +28,9 @@ struct DevState {
     int n_exits;          // exit records claimed (may exceed capacity; then FLAG_EXIT_OVERFLOW)
     unsigned status;
     int n_next;           // particles placed by the running step (summed by the tile scan)
-    int pad0;
+    float wmax;           // largest |weight| of the particles: the scale of the FP32 push's
+                          // fixed-point current (set by pic_init and pic_set_particles; kept
+                          // here, not in SimDev, so that batch copies of SimDev see updates)
     long long pad[4];
 };
 

@@ -35,6 +35,8 @@ struct Group {
     int inc_any, inc_segs, inc_rows;   // incident field on the grid: any member, x segments, rows
     int scan_blocks;                   // single simulation: blocks of the multi-block tile scan
     int cellscan_grid;                 // cell sort: blocks per simulation of the per-tile cell scan
+    const SimDev* one;                 // single simulation: its host descriptor, passed by value to the
+                                       // push (the same contents as sims[0]); nullptr for batches
 };
 
 // 3D field solver: columns of Y3_PX x Y3_PY points (x, y) marching along z through a
