@@ -73,7 +73,14 @@ INCIDENT_GRID = 0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from the
 # ncu capture summarised in profiles/ (kept in step with the kernel: set to None when the
 # kernel changes and until it is captured again)
-PROFILED_TRAFFIC = {("2d_lp_1024sq", "k_push<2,float>"): (116.5e6, "profiles/k_push_2d_lp_1024sq.md, step 760 (focus)")}
+PROFILED_TRAFFIC = {
+    ("2d_lp_1024sq", "k_push1<2,float>"): (111.5e6, "profiles/k_push_2d_lp_1024sq.md, step 762 (focus)"),
+    # the full 3D state (14 GB) is too large for a multi-pass capture: the box halved per axis
+    # (2.1 M electrons, step 233 at the focus), scaled by the electrons (x8): the push's traffic
+    # is per particle (record read and written) plus the grid per cell, both x8
+    ("3d_rp_512x256x256", "k_push1<3,float>"): (8 * 168.2e6, "profiles/k_push_3d_rp_256x128x128.md, box halved per "
+                                                             "axis at the focus, scaled x8 by electrons and cells"),
+}
 
 
 def workload(name):
@@ -307,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
     hbm_frac = by / push_s / 1e9 / hbm
     cells = w.n_cells
     yee_bytes = cells * (9 * es + 6 * es + 3 * es)           # read E, B, J; write E, B; clear J
-    kname = "k_push<%d,%s>" % (w.dim, "float" if es == 4 else "double")
+    kname = "k_push1<%d,%s>" % (w.dim, "float" if es == 4 else "double")   # one simulation: k_push1
     traffic = PROFILED_TRAFFIC.get((w.name, kname))
     roof = {"bound": "alu", "achieved": round(fl / push_s / 1e12, 3), "peak": round(alu_peak, 2),
             "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic[0] if traffic else None,
