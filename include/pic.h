@@ -316,7 +316,9 @@ typedef struct {
     int64_t fill_particles;  /* each quantum steps the resident simulations with the least
                                 remaining work (steps x electrons) first, adding more until
                                 this many electrons are in the batch (enough to fill the GPU);
-                                the others wait for the next quantum.  0: 6 000 000; < 0: all */
+                                the others wait for the next quantum.  A batch of one steps
+                                through that simulation's own step graph.  0: 2 000 000;
+                                < 0: all */
 } pic_serve_config;
 typedef struct {
     int32_t state;           /* 0 queued, 1 running, 2 done, -1 failed */

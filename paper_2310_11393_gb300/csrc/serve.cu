@@ -1,8 +1,9 @@
 // Continuous-batching request server (pic_serve_*): parameter-scan simulations arrive
 // at any time; a host scheduling thread admits queued requests whenever a resident
 // slot and device memory (estimated with pic_derive_params) are free, and each quantum
-// advances a batch of resident simulations together through the batched step (each
-// simulation stops exactly at its requested step count).  The batch is chosen shortest
+// advances a batch of resident simulations together through the batched step, or a batch
+// of one through its own step graph (each simulation stops exactly at its requested step
+// count).  The batch is chosen shortest
 // remaining work first (steps left x electrons) until it holds fill_particles electrons,
 // enough to fill the GPU: short requests finish early instead of sharing the device with
 // every long one to the end, and the device stays full.  Finished simulations retire
@@ -67,7 +68,7 @@ void pic_server::run()
     int64_t used = 0;
     const int max_res = cfg.max_resident > 0 ? cfg.max_resident : 256;
     const int quantum = cfg.quantum > 0 ? cfg.quantum : 50;
-    const int64_t fill = cfg.fill_particles > 0 ? cfg.fill_particles : (cfg.fill_particles < 0 ? -1 : 6000000);
+    const int64_t fill = cfg.fill_particles > 0 ? cfg.fill_particles : (cfg.fill_particles < 0 ? -1 : 2000000);
     for (;;) {
         // ---- admission (FIFO while memory and slots allow) ----
         std::vector<Request> admit;
@@ -134,7 +135,10 @@ void pic_server::run()
                 q = std::min(q, res[i].remaining);
                 list.push_back(res[i].sim);
             }
-        pic_status e = q > 0 ? pic_batch_step(list.data(), (int)list.size(), (int)q, st) : PIC_OK;
+        // one member: its own step graph (the single-simulation kernels); several: one batched
+        // launch per phase over all of them
+        pic_status e = PIC_OK;
+        if (q > 0) e = list.size() == 1 ? pic_step(list[0], (int)q, st) : pic_batch_step(list.data(), (int)list.size(), (int)q, st);
         cudaStreamSynchronize(st);
         // ---- bookkeeping and retirement ----
         std::vector<Resident> keep;
