@@ -568,7 +568,18 @@ def run_batch(args, rank=0, world=1, local_rank=0):
         secs = e0.elapsed_time(e1) * 1e-3
         n1 = sum(s.info().n_alive for s in sims)
         pushes, secs = job_totals(0.5 * (n0 + n1) * K, secs, world, dev)
-        out[mode] = {"pushes_per_s": pushes / secs, "seconds": secs}
+        # the same K steps once more, phase by phase (events between the phases; every
+        # phase launched on its own, so the sum exceeds the graph's step time)
+        if mode == "plain":
+            ph = np.zeros(5)
+            for s in sims:
+                ph += pic.pic_profile_step(s.h, K, stream)
+        else:
+            ph = pic.pic_batch_profile_step([s.h for s in sims], K, stream)
+        n2 = sum(s.info().n_alive for s in sims)
+        out[mode] = {"pushes_per_s": pushes / secs, "seconds": secs,
+                     "phases_ms_per_step": [round(x / K * 1e3, 4) for x in ph],
+                     "push_phase_pushes_per_s": 0.5 * (n1 + n2) * K / ph[0] if ph[0] > 0 else None}
         for s in sims:
             s.close()
     cells = sum(w.n_cells for w in ws_all)
@@ -584,6 +595,7 @@ def run_batch(args, rank=0, world=1, local_rank=0):
                        if args.autotune > 0 else "defaults",
                        "particles": int(sum(w.n_particles for w in ws_all)),
                        "sample": f"steps {args.warmup}..{args.warmup + K} of each 500-step run"},
+            "phases": ["push+deposit+placement", "tile scan", "cell-sort placement", "field solve", "step end"],
             "plain": out["plain"], "batched": out["batched"], "batched_over_plain": ratio}
 
 

@@ -307,6 +307,13 @@ pic_status pic_eval_incident(pic_sim* sim, int64_t n, const double* pts, double*
  * k the smallest sort_every among the members (counted per cached list). */
 pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, void* stream);
 
+/* Advances the same list n_steps steps like pic_batch_step, but launches each phase of the
+ * step (over every launch group of the list) one after another, with CUDA events recorded on
+ * `stream` between the phases, and returns in HOST seconds[5] the summed device time of each
+ * phase, as pic_profile_step.  Synchronous.  Used to compare the batched path with the plain
+ * one phase by phase. */
+pic_status pic_batch_profile_step(pic_sim** sims, int n_sims, int n_steps, void* stream, double* seconds);
+
 /* ---- serving: continuous batching of a request stream ----------------------------- */
 typedef struct pic_server pic_server;
 typedef struct {

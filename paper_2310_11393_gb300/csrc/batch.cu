@@ -220,10 +220,13 @@ void batch_forget(pic_sim* s)
     }
 }
 
-extern "C" pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, void* stream)
+namespace {
+// The cached entry of this exact list of simulations (built on first use); PIC_EINVAL for a
+// bad list.
+pic_status entry_of(pic_sim** sims, int n_sims, std::vector<pic_sim*>& key, BatchEntry** out)
 {
-    if (!sims || n_sims <= 0 || n_steps < 0) return PIC_EINVAL;
-    std::vector<pic_sim*> key(sims, sims + n_sims);
+    if (!sims || n_sims <= 0) return PIC_EINVAL;
+    key.assign(sims, sims + n_sims);
     for (pic_sim* s : key)
         if (!s) return PIC_EINVAL;
     {
@@ -234,31 +237,103 @@ extern "C" pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, vo
             return PIC_EINVAL;
         }
     }
-    BatchEntry* e = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        auto it = g_batches.find(key);
-        if (it != g_batches.end()) {
-            e = it->second;
-        } else {
-            std::string err;
-            pic_status r = build_entry(key, &e, err);
-            if (r != PIC_OK) {
-                key[0]->err = err;
-                return r;
-            }
-            g_batches[key] = e;
-        }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_batches.find(key);
+    if (it != g_batches.end()) {
+        *out = it->second;
+        return PIC_OK;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    // the graph starts at the push: the chunks are numbered by the previous step's end when
-    // that step was this list's, else here
+    std::string err;
+    BatchEntry* e = nullptr;
+    pic_status r = build_entry(key, &e, err);
+    if (r != PIC_OK) {
+        key[0]->err = err;
+        return r;
+    }
+    g_batches[key] = e;
+    *out = e;
+    return PIC_OK;
+}
+
+// before the first step of this list after anything else changed a member's layout: number
+// the work items of its launch groups
+void ensure_prefix(BatchEntry* e, const std::vector<pic_sim*>& key, cudaStream_t st)
+{
     bool fresh = true;
     for (pic_sim* s : key) fresh = fresh && s->prefix_group == e->id;
-    if (n_steps > 0 && !fresh) {
+    if (!fresh) {
         for (auto& gr : e->groups) sff::launch_prefix(gr.g, st);
         for (pic_sim* s : key) s->prefix_group = e->id;
     }
+}
+}  // namespace
+
+extern "C" pic_status pic_batch_profile_step(pic_sim** sims, int n_sims, int n_steps, void* stream, double* seconds)
+{
+    if (!seconds || n_steps < 0) return PIC_EINVAL;
+    std::vector<pic_sim*> key;
+    BatchEntry* e = nullptr;
+    pic_status r = entry_of(sims, n_sims, key, &e);
+    if (r != PIC_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < 5; ++i) seconds[i] = 0.0;
+    cudaEvent_t ev[6];
+    for (int i = 0; i < 6; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+            key[0]->err = "batch profile: event creation failed";
+            return PIC_ECUDA;
+        }
+    if (n_steps > 0) ensure_prefix(e, key, st);
+    for (int k = 0; k < n_steps && r == PIC_OK; ++k) {
+        bool sort = false;
+        if (e->sort_every > 0 && ++e->since_sort >= e->sort_every) {
+            e->since_sort = 0;
+            sort = true;
+        }
+        // the phases of every launch group one after another, the same launches as the graph
+        cudaEventRecord(ev[0], st);
+        for (auto& gr : e->groups) {
+            sff::launch_incident_grid(gr.g, st);
+            sff::launch_push(gr.g, sort, st);
+        }
+        cudaEventRecord(ev[1], st);
+        for (auto& gr : e->groups) sff::launch_scan(gr.g, st);
+        cudaEventRecord(ev[2], st);
+        if (sort)
+            for (auto& gr : e->groups) sff::launch_cell_sort(gr.g, st);
+        cudaEventRecord(ev[3], st);
+        for (auto& gr : e->groups) sff::launch_yee(gr.g, st);
+        cudaEventRecord(ev[4], st);
+        for (auto& gr : e->groups) sff::launch_step_end(gr.g, st);
+        cudaEventRecord(ev[5], st);
+        const cudaError_t ce = cudaEventSynchronize(ev[5]);
+        if (ce != cudaSuccess) {
+            key[0]->err = std::string("batch profiled step: ") + cudaGetErrorString(ce);
+            r = PIC_ECUDA;
+            break;
+        }
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            seconds[i] += 1e-3 * ms;
+        }
+    }
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+    return r;
+}
+
+extern "C" pic_status pic_batch_step(pic_sim** sims, int n_sims, int n_steps, void* stream)
+{
+    if (!sims || n_sims <= 0 || n_steps < 0) return PIC_EINVAL;
+    std::vector<pic_sim*> key;
+    BatchEntry* e = nullptr;
+    pic_status r = entry_of(sims, n_sims, key, &e);
+    if (r != PIC_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the graph starts at the push: the chunks are numbered by the previous step's end when
+    // that step was this list's, else here
+    if (n_steps > 0) ensure_prefix(e, key, st);
     for (int i = 0; i < n_steps; ++i) {
         bool sort = false;
         if (e->sort_every > 0 && ++e->since_sort >= e->sort_every) {

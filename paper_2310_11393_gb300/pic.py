@@ -122,6 +122,8 @@ def load():
     L.pic_eval_incident.argtypes = [P, c_int64, DP, DP, P]
     L.pic_autotune.restype = c_int
     L.pic_autotune.argtypes = [POINTER(pic_config), c_int, P, POINTER(c_double)]
+    L.pic_batch_profile_step.restype = c_int
+    L.pic_batch_profile_step.argtypes = [POINTER(P), c_int, c_int, P, POINTER(c_double)]
     L.pic_batch_step.restype = c_int
     L.pic_batch_step.argtypes = [POINTER(P), c_int, c_int, P]
     L.pic_serve_open.restype = c_int
@@ -271,6 +273,16 @@ def pic_batch_step(sims, n_steps: int, stream=0):
     arr = (c_void_p * len(sims))(*[s.value if isinstance(s, c_void_p) else s for s in sims])
     st = load().pic_batch_step(arr, len(sims), int(n_steps), c_void_p(stream))
     return check(st, sims[0])
+
+
+def pic_batch_profile_step(sims, n_steps: int, stream=0) -> np.ndarray:
+    """Phase times (push, tile scan, cell sort, field solve, step end; seconds) of n_steps
+    batched steps, each phase launched on its own."""
+    arr = (c_void_p * len(sims))(*[s.value if isinstance(s, c_void_p) else s for s in sims])
+    out = np.zeros(5)
+    check(load().pic_batch_profile_step(arr, len(sims), int(n_steps), c_void_p(stream),
+                                        out.ctypes.data_as(POINTER(c_double))))
+    return out
 
 
 def pic_serve_open(memory_budget=0, max_resident=0, quantum=0, fill_particles=0):

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synth
-from _support import field_errors, momentum_error
+from _support import field_errors, match_by_id, momentum_error
 
 pytestmark = pytest.mark.gpu
 
@@ -146,4 +146,26 @@ def test_alone_batch_and_profiled_steps_interleave(P):
     assert err < 1e-5, err
     assert field_errors(a.fields(), fr)[:6].max() < 1e-5
     for s in (a, b, c):
+        s.close()
+
+
+def test_batch_profile_equals_batched_steps(P):
+    """The phase-by-phase batched step (pic_batch_profile_step) advances the list exactly as the
+    batched graph does (FP64: the same kernels in the same order), and reports every phase."""
+    ws = [w.with_(precision=synth.FP64) for w in mix()[:3]]
+    a = [P.Simulation(P.config_from(w)) for w in ws]
+    b = [P.Simulation(P.config_from(w)) for w in ws]
+    P.pic_batch_step([s.h for s in a], 12)
+    P.pic_batch_step([s.h for s in b], 5)
+    ph = P.pic_batch_profile_step([s.h for s in b], 7)
+    assert ph[0] > 0 and ph[1] > 0 and ph[3] > 0 and ph[4] > 0
+    assert ph[2] < 0.1 * ph[0]          # no cell sort here: the events around an empty phase
+    for sa, sb in zip(a, b):
+        assert sb.info().step == 12
+        pa, pb = sa.particles(), sb.particles()
+        assert set(pa["id"].tolist()) == set(pb["id"].tolist())
+        common, ia, ib = match_by_id(pa, pb)
+        assert np.abs(pa["u"][ia] - pb["u"][ib]).max() < 1e-12 * max(1.0, np.abs(pa["u"]).max())
+        assert field_errors(sa.fields(), sb.fields()).max() < 1e-12
+    for s in a + b:
         s.close()
