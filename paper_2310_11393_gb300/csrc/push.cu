@@ -93,23 +93,26 @@ __device__ __forceinline__ R interp(const R* f, int bx, int bxy, const int b0, c
 }
 
 // Current accumulation in the work item's shared-memory box.  FP32: 32-bit fixed point with
-// the scale q = 2^30 / (N w_max) of the item (N particles): a contribution of one particle to
-// one node is bounded by w |v| <= w_max (Esirkepov's partial sums of the shape change are at
-// most the move in cells, v dt/dx, times dx/dt; the transverse weights are averages of shapes
-// in [0, 1]; |v| < c = 1), so no node's sum can leave the 32-bit range.  A shared-memory
-// integer add is one native reduction, where the FP32 add is a compare-and-swap loop with a
-// round trip per attempt.  The box is turned back into FP32 before its TMA reduce-add; the
-// rounding of each contribution to 1/q is below 2^-30 N w_max.  FP64 keeps double sums.
+// the scale q = 2^29 / (max(N, 256) w_max) of the item (N particles): a contribution of one
+// particle to one node is bounded by w |v| <= w_max (Esirkepov's partial sums of the shape
+// change are at most the move in cells, v dt/dx, times dx/dt; the transverse weights are
+// averages of shapes in [0, 1]; |v| < c = 1), so |c q| <= 2^21 and no node's sum leaves
+// 2^29.  Each contribution is rounded to the nearest integer by one FMA with 1.5 * 2^23 (the
+// sum lands in [2^23, 2^24), where the float spacing is 1: its low bits are the rounded
+// integer, exact for |c q| < 2^22) and added with the native shared-memory integer add (the
+// FP32 add is a compare-and-swap loop with a round trip per attempt); zero contributions are
+// added too (no test).  The box is turned back into FP32 before its TMA reduce-add; each
+// contribution's rounding is at most 2^-30 max(N, 256) w_max.  FP64 keeps double sums.
 __device__ __forceinline__ void jdep(float* a, float v, float q)
 {
-    const int iv = __float2int_rn(v * q);
-    if (iv != 0) atomicAdd(reinterpret_cast<int*>(a), iv);
+    const float f = fmaf(v, q, 12582912.0f);
+    atomicAdd(reinterpret_cast<int*>(a), __float_as_int(f) - 0x4B400000);
 }
 __device__ __forceinline__ void jdep(double* a, double v, double)
 {
     if (v != 0.0) atomicAdd(a, v);
 }
-constexpr float JQ_RANGE = 1073741824.0f;   // 2^30
+constexpr float JQ_RANGE = 536870912.0f;   // 2^29
 
 // Global chunk k of a launch group -> simulation, tile and particle slots.  Chunks are
 // numbered per simulation by the tile scan (ctile / crange) and across the group by gprefix.
@@ -372,7 +375,7 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
         const PhaseRef<R> pref = s_pref;
         // fixed-point scale of this item's current (FP32; unused in FP64)
         const float wmax = st->wmax;
-        const R jq = (sizeof(R) == 4 && wmax > 0.f) ? R(JQ_RANGE / ((float)(p1 - p0) * wmax)) : R(0);
+        const R jq = (sizeof(R) == 4 && wmax > 0.f) ? R(JQ_RANGE / ((float)max(p1 - p0, 256) * wmax)) : R(0);
         const R dtdx = bc.dtdx;
         const R jfac = bc.jfac;                     // -q dx/dt, q = -1
         const R hq = bc.hq;                         // q dt / 2
@@ -689,7 +692,7 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
         // ---- current flush and destination-tile counts ----
         if constexpr (sizeof(R) == 4) {
             // fixed point back to FP32, in place
-            const float inv = (float)(p1 - p0) * wmax * (1.0f / JQ_RANGE);
+            const float inv = (float)max(p1 - p0, 256) * wmax * (1.0f / JQ_RANGE);
             int* Jq = reinterpret_cast<int*>(Js);
             for (int i = tid; i < 3 * bvol; i += nth) Jq[i] = __float_as_int(__int2float_rn(Jq[i]) * inv);
             __syncthreads();
