@@ -196,10 +196,11 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
  * axis by dimension, then work items of 256..4096 particles at the best tile) it creates
  * the simulation on the current device and times two stretches, each trial_steps untimed
  * steps and then the faster of two runs of trial_steps timed steps (CUDA events on
- * `stream`): one from t = 0, one with its clock moved to the time the pulse is on the
- * plasma (focused beams: at the focus; plane wave: envelope centre at the slab centre) so
- * that the incident field and the deposit do their full work; the candidate's time is the
- * mean of the two.  It then destroys it; one
+ * `stream`): one from t = 0, one around the time the pulse is on the plasma (focused beams:
+ * at the focus; plane wave: envelope centre at the slab centre), reached by stepping when
+ * that takes at most 1500 steps (electrons heated by the pulse, as in the run) and else by
+ * moving the clock, so that the incident field and the deposit do their full work; the
+ * candidate's time is the mean of the two.  It then destroys it; one
  * candidate holds device memory at a time.  Candidates that do not fit (shared memory,
  * device memory) are skipped.  On success cfg->tile and cfg->chunk hold the fastest
  * choice and *ms_per_step (may be NULL) its time per step.  Only tile/chunk entries left

@@ -55,13 +55,13 @@ def match_by_id(a, b):
 # evaluation is nearly the same at neighbouring points, so an electron's momentum error
 # grows by ~dt * 1.2e-6 a0 per step whatever |p| is at that instant (electrons without any
 # plasma response show the same error as full runs).  Hence:
-#   * the spec bar, relative 1e-5 normalised by max(|p|, a0) (a0 the quiver-momentum
+#   * the target bar, relative 1e-5 normalised by max(|p|, a0) (a0 the quiver-momentum
 #     scale), as long as the accumulated impulse error N dt EPS_INC stays below it, and that
 #     impulse error after (3D RP at a0 = 20: 1.05e-5 measured at step 40, bar 1.15e-5);
 #   * per particle against max(|p_ref|, 1e-2 a0) (the tighter reading), bounded by
 #     1e-5 + N dt EPS_INC / 1e-2;
-# with EPS_INC = 2e-6 of the amplitude.  The survey's first reading (floor 1e-3 a0) is
-# printed beside them.
+# with EPS_INC = 2e-6 of the amplitude.  The tightest reading (floor 1e-3 a0) is printed
+# beside them.
 MOMENTUM_FLOOR = 1.0
 TIGHT_FLOOR = 1e-2
 EPS_INC = 2e-6

@@ -15,8 +15,8 @@ the accumulated impulse error of the FP32 incident field once that is larger; pe
 against max(|p_ref|, 1e-2 a0) within 1e-5 plus that impulse error; per component
 max |F_gpu - F_ref| <= 1e-5 max |F_ref| (3D: 1e-4, the fields following the electrons' FP32
 trajectories in the a0 = 20 focus); FP64 1e-9 for all, the momenta against
-max(|p_ref|, 1e-3 a0).  The survey's first reading of the
-momentum metric (floor 1e-3 a0) is printed beside them.
+max(|p_ref|, 1e-3 a0).  The tightest reading of the momentum metric (floor 1e-3 a0) is
+printed beside them.
 
 Whole runs at the same configurations (1500 and 1200 steps, the workloads' own lengths):
 energies every 50 steps to 1e-3 and the Kolmogorov-Smirnov distance of the electron energy

@@ -1,6 +1,6 @@
 """CUDA path (through the C-ABI) against the FP64 oracle on the same seeded inputs.
 
-Tolerances (the spec bar, made concrete):
+Tolerances (the target's relative 1e-5, made concrete):
   * FP32 runs, first 50 steps: |p_gpu - p_ref| / max(|p_ref|, a0) <= 1e-5, a0 being the
     quiver-momentum scale, or the accumulated impulse error of the single-precision incident
     field once that is larger (~1.2e-6 of its amplitude per evaluation, nearly the same at
