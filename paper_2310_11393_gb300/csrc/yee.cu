@@ -16,6 +16,8 @@
 // reads in the same launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "beam.cuh"
 #include "sff_common.cuh"
 #include "sff_kernels.h"
@@ -48,9 +50,12 @@ __device__ __forceinline__ bool has_point(const SimDev& S, int comp, const int g
     return true;
 }
 
-template <int D, typename R, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, const Work* __restrict__ work,
-                                             int nwork, int* __restrict__ counter)
+// ONE: the launch is one simulation whose descriptor `one` is a kernel parameter (its
+// fields come from the constant bank and its tensor maps are used from parameter space,
+// with no acquire); otherwise the descriptors are read from the device array `sims`.
+template <int D, typename R, int TX, int TY, int TZ, bool ONE>
+__device__ __forceinline__ void yee_body(const SimDev* __restrict__ sims, const SimDev& one,
+                                         const Work* __restrict__ work, int nwork, int* __restrict__ counter)
 {
     constexpr int HX = 4, HY = D > 1 ? 2 : 0, HZ = D > 2 ? 2 : 0;
     constexpr int EX = TX + 2 * HX, EY = TY + 2 * HY, EZ = TZ + 2 * HZ;
@@ -95,13 +100,13 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
     auto issue = [&](int it, int b) {
         if (tid != 0) return;
         const Work w = work[it];
-        const SimDev& S = sims[w.sim];
+        const SimDev& S = ONE ? one : sims[w.sim];
         int l[3];
         tile_lo(S, w.tile, l);
         const int o[3] = {l[0] - HX + G, D > 1 ? l[1] - HY + G : 0, D > 2 ? l[2] - HZ + G : 0};
         const int p = S.st->parity;
         // one acquire per simulation and block (the maps were written before the launch)
-        if (w.sim != acq_sim) {
+        if (!ONE && w.sim != acq_sim) {
             tensormap_acquire(&S.tm_yin);
             tensormap_acquire(&S.tm_yj);
             tensormap_acquire(&S.tm_yout);
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
         R* Ny = Jn + BV;
         R* Nz = Jn + 2 * BV;
         const Work wk = work[item];
-        const SimDev& S = sims[wk.sim];
+        const SimDev& S = ONE ? one : sims[wk.sim];
         DevState* st = S.st;
         const int par = st->parity;
         int lo[3];
@@ -307,6 +312,20 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
     if (tid == 0) bulk_wait0();
 }
 
+template <int D, typename R, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+                                             int nwork, int* __restrict__ counter)
+{
+    yee_body<D, R, TX, TY, TZ, false>(sims, *sims, work, nwork, counter);
+}
+
+template <int D, typename R, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) k_yee1(const __grid_constant__ SimDev one, const Work* __restrict__ work,
+                                              int nwork, int* __restrict__ counter)
+{
+    yee_body<D, R, TX, TY, TZ, true>(nullptr, one, work, nwork, counter);
+}
+
 // ---------------------------------------------------------------------------------
 // 3D: a work item is a column of PX x PY points (x, y) over a segment [z0, z1) of planes.
 // The column marches along z; plane k of E, B and J_p (box x: 4 points of halo on each
@@ -321,9 +340,9 @@ __global__ void __launch_bounds__(256) k_yee(const SimDev* __restrict__ sims, co
 // y in [y0-1, y0+PY] and planes from z0-1: one more than the outputs need on the low
 // side, so that every face point's Mur neighbour (one point inwards) is on hand.
 // ---------------------------------------------------------------------------------
-template <typename R, int PX, int PY, int NS, int NT>
-__global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, const Work* __restrict__ work,
-                                              int nwork, int* __restrict__ counter)
+template <typename R, int PX, int PY, int NS, int NT, bool ONE>
+__device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, const SimDev& one,
+                                           const Work* __restrict__ work, int nwork, int* __restrict__ counter)
 {
     constexpr int TV = PX * PY;
     constexpr int BX = PX + 8, BY = PY + 4, BV = BX * BY;
@@ -334,7 +353,9 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
     constexpr size_t OOFF = NOFF + round128(6 * BV * sizeof(R));
     constexpr int AW = PX + 3, AH = PY + 3;      // Bh range: box x 2 .. PX+4, y 0 .. PY+2
     constexpr int NW = PX + 2, NH = PY + 2;      // N range:  box x 3 .. PX+4, y 1 .. PY+2
-    static_assert(NT >= TV && NT >= NW * NH, "one pass of B and D per plane");
+    constexpr int NA = AW * AH;
+    constexpr int NR = (NA + NT - 1) / NT;       // Bh points per thread
+    static_assert((NS & (NS - 1)) == 0, "a ring of a power-of-two number of stages");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ int s_item;
@@ -348,6 +369,20 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
     R* Hr = reinterpret_cast<R*>(smem_raw + HOFF);     // [3][3][BY][BX]  Bh ring
     R* Nr = reinterpret_cast<R*>(smem_raw + NOFF);     // [2][3][BY][BX]  N ring
     R* Outb = reinterpret_cast<R*>(smem_raw + OOFF);   // [2][6][PY][PX]
+    // Every phase of a plane works on the thread's own points of the Bh range, a = tid + r NT
+    // (box x 2 + a % AW, y a / AW): Bh on all of them, N on those in the N range, the
+    // outputs (box x 4 .. PX+3, y 2 .. PY+1) on those in the tile.  Their box indices and
+    // output slots are fixed for the launch.
+    int pidx[NR], pout[NR];
+    bool pN[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int a = tid + r * NT;
+        const int lx = 2 + a % AW, ly = a / AW;
+        pidx[r] = a < NA ? lx + BX * ly : -1;
+        pN[r] = a < NA && lx >= 3 && ly >= 1;
+        pout[r] = (a < NA && lx >= 4 && lx < PX + 4 && ly >= 2 && ly < PY + 2) ? (lx - 4) + PX * (ly - 2) : -1;
+    }
     uint32_t ph = 0;      // mbarrier phase of each stage
     int oslot = 0;
     for (;;) {
@@ -357,9 +392,10 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
         __syncthreads();
         if (item >= nwork) break;
         const Work wk = work[item];
-        const SimDev& S = sims[wk.sim];
+        const SimDev& S = ONE ? one : sims[wk.sim];
         DevState* st = S.st;
         const int par = st->parity;
+        const int n0 = S.n[0], n1 = S.n[1], n2 = S.n[2];
         int t = wk.tile;
         const int cx = t % S.nyt[0];
         t /= S.nyt[0];
@@ -367,12 +403,28 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
         const int cz = t / S.nyt[1];
         const int x0 = cx * PX, y0 = cy * PY;
         const int z0 = cz * S.yt[2];
-        const int z1 = min(z0 + S.yt[2], S.n[2] + 1);
+        const int z1 = min(z0 + S.yt[2], n2 + 1);
         const int pa = z0 - 2, plast = z1 + 1;     // planes loaded
-        const bool col_int = x0 > 0 && x0 + PX < S.n[0] && y0 > 0 && y0 + PY < S.n[1];
+        const bool col_int = x0 > 0 && x0 + PX < n0 && y0 > 0 && y0 + PY < n1;
         const YeeC<R>& yc = yee_of<R>(S);
         const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
-        auto stage_of = [&](int p) { return (p - pa) % NS; };
+        const long long sz = S.sz, sc = S.sc;
+        // per point of the column: bit 0 x on a face (0 or n_x), 1 y on a face, 2 x in
+        // [0, n_x - 1], 3 x in [0, n_x], 4 y in [0, n_y - 1], 5 y in [0, n_y]; and the output
+        // points' J_{1-p} (cleared for the next step's deposit) on plane -G
+        unsigned pm[NR];
+        R* jrow[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int a = tid + r * NT;
+            const int gx = x0 - 4 + 2 + a % AW, gy = y0 - 2 + a / AW;
+            pm[r] = (gx == 0 || gx == n0 ? 1u : 0u) | (gy == 0 || gy == n1 ? 2u : 0u) |
+                    (gx >= 0 && gx <= n0 - 1 ? 4u : 0u) | (gx >= 0 && gx <= n0 ? 8u : 0u) |
+                    (gy >= 0 && gy <= n1 - 1 ? 16u : 0u) | (gy >= 0 && gy <= n1 ? 32u : 0u);
+            jrow[r] = reinterpret_cast<R*>(S.F) + (long long)comp_j(1 - par) * sc + (long long)(gy + G) * S.sy +
+                      (gx + G);
+        }
+        auto stage_of = [&](int p) { return (p - pa) & (NS - 1); };
         auto Hs = [&](int p) { return Hr + ((p - pa) % 3) * 3 * BV; };
         auto Ns = [&](int p) { return Nr + ((p - pa) & 1) * 3 * BV; };
         auto issue = [&](int p) {
@@ -383,14 +435,15 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
             tma_load_box<3>(reinterpret_cast<unsigned char*>(In(sgi)) + JOFF, &S.tm_yj, org, comp_j(par), &bars[sgi]);
         };
         if (tid == 0) {
-            tensormap_acquire(&S.tm_yin);
-            tensormap_acquire(&S.tm_yj);
-            tensormap_acquire(&S.tm_yout);
+            if (!ONE) {
+                tensormap_acquire(&S.tm_yin);
+                tensormap_acquire(&S.tm_yj);
+                tensormap_acquire(&S.tm_yout);
+            }
             for (int p = pa; p <= min(pa + NS - 1, plast); ++p) issue(p);
         }
         int pissued = min(pa + NS - 1, plast);
         int pw = pa - 1;      // last plane waited for
-
         // Mur faces of plane m (every point of the N range on a face, fewer faces first).
         // Off the z faces only the lines x = 0, n_x and y = 0, n_y of the column are visited
         // (a point on two lines is written twice, with the same value).
@@ -443,6 +496,7 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
             }
         };
 
+
         bool failed = false;
         for (int q = z0 - 3; q <= z1; ++q) {
             bool ok = true;
@@ -452,18 +506,26 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
                 ok = ok && mbar_wait_bounded(&bars[sgi], (ph >> sgi) & 1u);
                 ph ^= 1u << sgi;
             }
-            // S1: A(q+1) and D(q-1)
+            // S1: A(q+1) and D(q-1) on the thread's points
             const bool doA = q + 1 <= z1, doD = q - 1 >= z0;
             if (doA || doD) {
                 const int m = q - 1;
-                for (int u = tid; u < TV + AW * AH; u += NT) {
-                    if (u < TV) {
-                        if (!doD) continue;
-                        const R* H0 = Hs(m);
-                        const R* N0 = Ns(m);
-                        const R* N1 = Ns(m + 1);
-                        const int tx = u % PX, ty = u / PX;
-                        const int i = (tx + 4) + BX * (ty + 2);
+                const R* I0 = In(stage_of(q + 1));
+                const R* I1 = In(stage_of(q + 2));
+                R* Ha = doA ? Hs(q + 1) : Hr;
+                const R* H0 = doD ? Hs(m) : Hr;
+                const R* N0 = Ns(m + 2);
+                const R* N1 = Ns(m + 1);
+                R* Out = Outb + oslot * 6 * TV;
+                // every output point of the plane has all six components
+                const bool zint = col_int && m >= 1 && m <= n2 - 1;
+                const bool zs = m >= 0 && m <= n2 - 1, zn = m >= 0 && m <= n2;
+                const long long zoff = (long long)(m + G) * sz;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int i = pidx[r];
+                    if (i < 0) continue;
+                    if (doD && pout[r] >= 0) {
                         const R dNz_dy = N0[2 * BV + i + BX] - N0[2 * BV + i];
                         const R dNx_dy = N0[i + BX] - N0[i];
                         const R dNy_dz = N1[BV + i] - N0[BV + i];
@@ -472,38 +534,35 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
                         const R dNy_dx = N0[BV + i + 1] - N0[BV + i];
                         R v[6] = {N0[i], N0[BV + i], N0[2 * BV + i], H0[i] - hc * (dNz_dy - dNy_dz),
                                   H0[BV + i] - hc * (dNx_dz - dNz_dx), H0[2 * BV + i] - hc * (dNy_dx - dNx_dy)};
-                        if (!(col_int && m >= 1 && m <= S.n[2] - 1)) {
-                            const int g[3] = {x0 + tx, y0 + ty, m};
-#pragma unroll
-                            for (int c = 0; c < 6; ++c)
-                                if (!has_point<3>(S, c, g)) v[c] = R(0);
+                        if (!zint) {
+                            const unsigned b = pm[r];
+                            const bool xs = b & 4u, xn = b & 8u, ys = b & 16u, yn = b & 32u;
+                            if (!(xs && yn && zn)) v[0] = R(0);
+                            if (!(xn && ys && zn)) v[1] = R(0);
+                            if (!(xn && yn && zs)) v[2] = R(0);
+                            if (!(xn && ys && zs)) v[3] = R(0);
+                            if (!(xs && yn && zs)) v[4] = R(0);
+                            if (!(xs && ys && zn)) v[5] = R(0);
                         }
-                        R* Out = Outb + oslot * 6 * TV;
+                        const int u = pout[r];
 #pragma unroll
                         for (int c = 0; c < 6; ++c) Out[c * TV + u] = v[c];
                         // clear J_{1-p} on plane m (the next step deposits into it)
-                        R* Fg = reinterpret_cast<R*>(S.F);
-                        const long long jb = (long long)comp_j(1 - par) * S.sc + (long long)(m + G) * S.sz +
-                                             (long long)(y0 + ty + G) * S.sy + (x0 + tx + G);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) Fg[jb + c * S.sc] = R(0);
-                    } else {
-                        if (!doA) continue;
-                        const int k = u - TV;
-                        const R* I0 = In(stage_of(q + 1));
-                        const R* I1 = In(stage_of(q + 2));
-                        R* Hc = Hs(q + 1);
-                        const int lx = 2 + k % AW, ly = k / AW;
-                        const int i = lx + BX * ly;
+                        R* jp = jrow[r] + zoff;
+                        jp[0] = R(0);
+                        jp[sc] = R(0);
+                        jp[2 * sc] = R(0);
+                    }
+                    if (doA) {
                         const R dEz_dy = I0[2 * BV + i + BX] - I0[2 * BV + i];
                         const R dEx_dy = I0[i + BX] - I0[i];
                         const R dEy_dz = I1[BV + i] - I0[BV + i];
                         const R dEx_dz = I1[i] - I0[i];
                         const R dEz_dx = I0[2 * BV + i + 1] - I0[2 * BV + i];
                         const R dEy_dx = I0[BV + i + 1] - I0[BV + i];
-                        Hc[i] = I0[3 * BV + i] - hc * (dEz_dy - dEy_dz);
-                        Hc[BV + i] = I0[4 * BV + i] - hc * (dEx_dz - dEz_dx);
-                        Hc[2 * BV + i] = I0[5 * BV + i] - hc * (dEy_dx - dEx_dy);
+                        Ha[i] = I0[3 * BV + i] - hc * (dEz_dy - dEy_dz);
+                        Ha[BV + i] = I0[4 * BV + i] - hc * (dEx_dz - dEz_dx);
+                        Ha[2 * BV + i] = I0[5 * BV + i] - hc * (dEy_dx - dEx_dy);
                     }
                 }
             }
@@ -520,18 +579,20 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
                 }
                 oslot ^= 1;
             }
-            // S2: B(q+1), then its Mur faces
+            // S2: B(q+1) on the thread's points of the N range, then its Mur faces
             const int b = q + 1;
             if (b >= z0 - 1 && b <= z1) {
-                const bool faces = !col_int || b == 0 || b == S.n[2];
+                const bool fz = b == 0 || b == n2;
+                const bool faces = !col_int || fz;
                 const R* I0 = In(stage_of(b));
                 const R* J0 = I0 + JOFF / sizeof(R);
                 const R* Hc = Hs(b);
-                const R* Hp = Hs(b - 1);
+                const R* Hp = Hs(b + 2);      // plane b-1 (a ring of three)
                 R* Nc = Ns(b);
-                for (int k = tid; k < NW * NH; k += NT) {
-                    const int lx = 3 + k % NW, ly = 1 + k / NW;
-                    const int i = lx + BX * ly;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (!pN[r]) continue;
+                    const int i = pidx[r];
                     const R dBz_dy = Hc[2 * BV + i] - Hc[2 * BV + i - BX];
                     const R dBx_dy = Hc[i] - Hc[i - BX];
                     const R dBy_dz = Hc[BV + i] - Hp[BV + i];
@@ -546,10 +607,10 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
                         Nc[BV + i] = ey;
                         Nc[2 * BV + i] = ez;
                     } else {
-                        const int g[3] = {x0 - 4 + lx, y0 - 2 + ly, b};
-                        if (!face_axes<3>(S, 0, g)) Nc[i] = ex;
-                        if (!face_axes<3>(S, 1, g)) Nc[BV + i] = ey;
-                        if (!face_axes<3>(S, 2, g)) Nc[2 * BV + i] = ez;
+                        const bool fx = pm[r] & 1u, fy = pm[r] & 2u;
+                        if (!(fy || fz)) Nc[i] = ex;
+                        if (!(fx || fz)) Nc[BV + i] = ey;
+                        if (!(fx || fy)) Nc[2 * BV + i] = ez;
                     }
                 }
                 // the store of two planes back has read its buffer (reused by the next D)
@@ -585,6 +646,20 @@ __global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, c
     if (tid == 0) bulk_wait0();
 }
 
+template <typename R, int PX, int PY, int NS, int NT>
+__global__ void __launch_bounds__(NT) k_yee3s(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+                                              int nwork, int* __restrict__ counter)
+{
+    yee3s_body<R, PX, PY, NS, NT, false>(sims, *sims, work, nwork, counter);
+}
+
+template <typename R, int PX, int PY, int NS, int NT>
+__global__ void __launch_bounds__(NT) k_yee3s1(const __grid_constant__ SimDev one, const Work* __restrict__ work,
+                                               int nwork, int* __restrict__ counter)
+{
+    yee3s_body<R, PX, PY, NS, NT, true>(nullptr, one, work, nwork, counter);
+}
+
 // 1D/2D field-solver tiles (must match the host's tile choice)
 template <int D>
 struct YeeTile;
@@ -600,25 +675,46 @@ struct YeeTile<2> {
 template <int D, typename R>
 static void yee_t(const Group& g, cudaStream_t s)
 {
-    if constexpr (D == 3)
-        k_yee3s<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>
-            <<<g.yee_grid, Y3_NT, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
-    else
-        k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
-            <<<g.yee_grid, 256, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    if constexpr (D == 3) {
+        if (g.one)
+            k_yee3s1<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>
+                <<<g.yee_grid, Y3_NT, g.yee_smem, s>>>(*g.one, g.ywork, g.nywork, g.counters + 2);
+        else
+            k_yee3s<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>
+                <<<g.yee_grid, Y3_NT, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    } else {
+        if (g.one)
+            k_yee1<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
+                <<<g.yee_grid, 256, g.yee_smem, s>>>(*g.one, g.ywork, g.nywork, g.counters + 2);
+        else
+            k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
+                <<<g.yee_grid, 256, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    }
 }
 
 template <int D, typename R>
 static void attr_yee(size_t smem, int* out)
 {
+    // both forms of the kernel get the shared-memory size; the occupancy (which sizes the
+    // grid) is the lower of the two
     if constexpr (D == 3) {
         auto k = k_yee3s<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>;
+        auto k1 = k_yee3s1<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>;
+        int b1 = 0;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, Y3_NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k1, Y3_NT, smem);
+        *out = std::min(*out, b1);
     } else {
         auto k = k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>;
+        auto k1 = k_yee1<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>;
+        int b1 = 0;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, 256, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k1, 256, smem);
+        *out = std::min(*out, b1);
     }
 }
 
