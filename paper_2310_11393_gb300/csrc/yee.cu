@@ -420,7 +420,8 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
             const int gx = x0 - 4 + 2 + a % AW, gy = y0 - 2 + a / AW;
             pm[r] = (gx == 0 || gx == n0 ? 1u : 0u) | (gy == 0 || gy == n1 ? 2u : 0u) |
                     (gx >= 0 && gx <= n0 - 1 ? 4u : 0u) | (gx >= 0 && gx <= n0 ? 8u : 0u) |
-                    (gy >= 0 && gy <= n1 - 1 ? 16u : 0u) | (gy >= 0 && gy <= n1 ? 32u : 0u);
+                    (gy >= 0 && gy <= n1 - 1 ? 16u : 0u) | (gy >= 0 && gy <= n1 ? 32u : 0u) |
+                    (gx == 0 ? 64u : 0u) | (gy == 0 ? 128u : 0u);
             jrow[r] = reinterpret_cast<R*>(S.F) + (long long)comp_j(1 - par) * sc + (long long)(gy + G) * S.sy +
                       (gx + G);
         }
@@ -579,7 +580,8 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
                 }
                 oslot ^= 1;
             }
-            // S2: B(q+1) on the thread's points of the N range, then its Mur faces
+            // S2: B(q+1) on the thread's points of the N range, with the Mur condition on the
+            // x and y faces; on the z faces the passes of mur_plane follow
             const int b = q + 1;
             if (b >= z0 - 1 && b <= z1) {
                 const bool fz = b == 0 || b == n2;
@@ -589,34 +591,64 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
                 const R* Hc = Hs(b);
                 const R* Hp = Hs(b + 2);      // plane b-1 (a ring of three)
                 R* Nc = Ns(b);
+                // E^{n+1} component c at box point j (backward differences of Bh)
+                auto enew = [&](int c, int j) -> R {
+                    if (c == 0) {
+                        const R dBz_dy = Hc[2 * BV + j] - Hc[2 * BV + j - BX];
+                        const R dBy_dz = Hc[BV + j] - Hp[BV + j];
+                        return I0[j] + cdt * (dBz_dy - dBy_dz) - dt * J0[j];
+                    } else if (c == 1) {
+                        const R dBx_dz = Hc[j] - Hp[j];
+                        const R dBz_dx = Hc[2 * BV + j] - Hc[2 * BV + j - 1];
+                        return I0[BV + j] + cdt * (dBx_dz - dBz_dx) - dt * J0[BV + j];
+                    }
+                    const R dBy_dx = Hc[BV + j] - Hc[BV + j - 1];
+                    const R dBx_dy = Hc[j] - Hc[j - BX];
+                    return I0[2 * BV + j] + cdt * (dBy_dx - dBx_dy) - dt * J0[2 * BV + j];
+                };
+                // first-order Mur at face point j of component c from the inward neighbour nb
+                // (E^n from the stage, E^{n+1} of the neighbour given)
+                auto mur = [&](int c, int j, int nb, R en_nb) -> R {
+                    return I0[c * BV + nb] + km * (en_nb - I0[c * BV + j]);
+                };
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     if (!pN[r]) continue;
                     const int i = pidx[r];
-                    const R dBz_dy = Hc[2 * BV + i] - Hc[2 * BV + i - BX];
-                    const R dBx_dy = Hc[i] - Hc[i - BX];
-                    const R dBy_dz = Hc[BV + i] - Hp[BV + i];
-                    const R dBx_dz = Hc[i] - Hp[i];
-                    const R dBz_dx = Hc[2 * BV + i] - Hc[2 * BV + i - 1];
-                    const R dBy_dx = Hc[BV + i] - Hc[BV + i - 1];
-                    const R ex = I0[i] + cdt * (dBz_dy - dBy_dz) - dt * J0[i];
-                    const R ey = I0[BV + i] + cdt * (dBx_dz - dBz_dx) - dt * J0[BV + i];
-                    const R ez = I0[2 * BV + i] + cdt * (dBy_dx - dBx_dy) - dt * J0[2 * BV + i];
-                    if (!faces) {
+                    const R ex = enew(0, i), ey = enew(1, i), ez = enew(2, i);
+                    const unsigned f = pm[r];
+                    const bool fx = f & 1u, fy = f & 2u;
+                    if (!faces || (!fx && !fy && !fz)) {
                         Nc[i] = ex;
                         Nc[BV + i] = ey;
                         Nc[2 * BV + i] = ez;
-                    } else {
-                        const bool fx = pm[r] & 1u, fy = pm[r] & 2u;
+                    } else if (fz) {
+                        // z faces: every face point is left to mur_plane
                         if (!(fy || fz)) Nc[i] = ex;
                         if (!(fx || fz)) Nc[BV + i] = ey;
                         if (!(fx || fy)) Nc[2 * BV + i] = ez;
+                    } else {
+                        // x / y faces (points on fewer faces first, along the lowest face axis:
+                        // Ez on an x-y edge takes its x neighbour's value on the y face)
+                        const int sx = (f & 64u) ? 1 : -1, sy = (f & 128u) ? BX : -BX;
+                        Nc[i] = fy ? mur(0, i, i + sy, enew(0, i + sy)) : ex;
+                        Nc[BV + i] = fx ? mur(1, i, i + sx, enew(1, i + sx)) : ey;
+                        R vz = ez;
+                        if (fx && fy) {
+                            const int nb = i + sx;
+                            vz = mur(2, i, nb, mur(2, nb, nb + sy, enew(2, nb + sy)));
+                        } else if (fx) {
+                            vz = mur(2, i, i + sx, enew(2, i + sx));
+                        } else if (fy) {
+                            vz = mur(2, i, i + sy, enew(2, i + sy));
+                        }
+                        Nc[2 * BV + i] = vz;
                     }
                 }
                 // the store of two planes back has read its buffer (reused by the next D)
                 if (tid == 0) bulk_wait_read1();
                 __syncthreads();
-                if (faces && b != 0) mur_plane(b);
+                if (fz && b != 0) mur_plane(b);
                 if (b == 1 && z0 <= 1) mur_plane(0);
             } else {
                 if (tid == 0) bulk_wait_read1();
