@@ -81,7 +81,7 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         long long nyw = 0, nch = 0;
         size_t psm = 0, ysm = 0;
         for (int i : mem) {
-            nyw += sims[i]->h.nytiles;
+            nyw += sims[i]->nywork;
             nch += sims[i]->h.max_chunks;
             psm = std::max(psm, sims[i]->grp.push_smem);
             ysm = std::max(ysm, sims[i]->grp.yee_smem);
@@ -115,7 +115,8 @@ pic_status build_entry(const std::vector<pic_sim*>& sims, BatchEntry** out, std:
         for (int k = 0; k < n; ++k) {
             pic_sim* s = sims[mem[k]];
             hs[k] = s->h;
-            for (int t = 0; t < s->h.nytiles; ++t) yw.push_back({k, t});
+            for (int t = 0; t < s->h.nytiles; ++t)
+                if (yee_tile_active(s->h, s->cfg.dim, t)) yw.push_back({k, t});
         }
         cudaMemcpy(d_sims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice);
         cudaMemcpy(d_yw, yw.data(), sizeof(Work) * nyw, cudaMemcpyHostToDevice);

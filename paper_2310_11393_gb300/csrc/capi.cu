@@ -783,8 +783,10 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     INIT_CHECK(cudaMemcpyAsync(s->d, &h, sizeof h, cudaMemcpyHostToDevice, st));
     // work lists of the single-simulation group
     {
-        std::vector<Work> yw(L.nytiles);
-        for (int i = 0; i < L.nytiles; ++i) yw[i] = {0, i};
+        std::vector<Work> yw;
+        for (int i = 0; i < L.nytiles; ++i)
+            if (yee_tile_active(h, cfg->dim, i)) yw.push_back({0, i});
+        s->nywork = (int)yw.size();
         INIT_CHECK(cudaMemcpyAsync(s->d_ywork, yw.data(), yw.size() * sizeof(Work), cudaMemcpyHostToDevice, st));
         INIT_CHECK(cudaMemsetAsync(s->d_gprefix, 0, 64, st));
         INIT_CHECK(cudaStreamSynchronize(st));
@@ -821,7 +823,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     g.one = &s->h;       // the same descriptor, by value for the push (final from here on)
     g.gprefix = s->d_gprefix;
     g.ywork = s->d_ywork;
-    g.nywork = L.nytiles;
+    g.nywork = s->nywork;
     g.nsims = 1;
     g.counters = s->d_counters;
     g.dim = cfg->dim;
@@ -842,7 +844,7 @@ pic_status pic_init(const pic_config* cfg_in, const pic_allocator* alloc, void* 
     g.inc_segs = (cfg->n[0] + 1 + 255) / 256;
     g.inc_rows = (cfg->dim > 1 ? cfg->n[1] + 1 : 1) * (cfg->dim > 2 ? cfg->n[2] + 1 : 1);
     g.push_grid = std::max(1, std::min(L.max_chunks, bp * nsm));
-    g.yee_grid = std::max(1, std::min(L.nytiles, by * nsm));
+    g.yee_grid = std::max(1, std::min(s->nywork, by * nsm));
     g.scatter_grid = std::max(1, std::min(L.max_chunks, bs * nsm));
     INIT_CHECK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     INIT_CHECK(cudaStreamCreateWithFlags(&s->cap_stream2, cudaStreamNonBlocking));

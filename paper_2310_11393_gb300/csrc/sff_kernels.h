@@ -93,6 +93,16 @@ void launch_eval_incident(const SimDev* sim, int dim, int prec, long long n, con
 // streaming multiprocessors of the current device (queried once per device)
 int device_sms();
 
+// Is field-solver tile t a work item?  In 3D a column whose first point lies on the node
+// plane x = n_x (or y = n_y), which holds nothing else, is not: the column before it writes
+// that plane of E and B and clears its J.
+inline bool yee_tile_active(const SimDev& h, int dim, int t)
+{
+    if (dim != 3) return true;
+    const int cx = t % h.nyt[0], cy = (t / h.nyt[0]) % h.nyt[1];
+    return cx * h.yt[0] != h.n[0] && cy * h.yt[1] != h.n[1];
+}
+
 // kernel attributes (dynamic shared memory opt-in); returns blocks per SM
 int prepare_push(int dim, int prec, size_t smem);
 int prepare_yee(int dim, int prec, size_t smem);

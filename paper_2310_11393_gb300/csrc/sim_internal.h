@@ -44,6 +44,7 @@ struct pic_sim {
     // single-simulation launch group
     Group grp{};
     Work* d_ywork = nullptr;
+    int nywork = 0;              // field-solver work items (yee_tile_active)
     int* d_gprefix = nullptr;    // chunk numbering of the single-simulation group
     int* d_counters = nullptr;
     double* d_acc = nullptr;     // 8 doubles

@@ -410,18 +410,23 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
         const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
         const long long sz = S.sz, sc = S.sc;
         // per point of the column: bit 0 x on a face (0 or n_x), 1 y on a face, 2 x in
-        // [0, n_x - 1], 3 x in [0, n_x], 4 y in [0, n_y - 1], 5 y in [0, n_y]; and the output
-        // points' J_{1-p} (cleared for the next step's deposit) on plane -G
+        // [0, n_x - 1], 3 x in [0, n_x], 4 y in [0, n_y - 1], 5 y in [0, n_y], 6 x = 0,
+        // 7 y = 0, 8 an output past the tile: the column ends at x = n_x (y = n_y) and no
+        // column starts there, so this one also writes the node plane x = n_x (y = n_y);
+        // and the point's J_{1-p} (cleared for the next step's deposit) on plane -G
+        const bool xend = x0 + PX == n0, yend = y0 + PY == n1;
         unsigned pm[NR];
         R* jrow[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int a = tid + r * NT;
             const int gx = x0 - 4 + 2 + a % AW, gy = y0 - 2 + a / AW;
+            const bool past = (xend && gx == n0 && gy >= y0 && gy <= y0 + PY - (yend ? 0 : 1)) ||
+                              (yend && gy == n1 && gx >= x0 && gx <= x0 + PX - (xend ? 0 : 1));
             pm[r] = (gx == 0 || gx == n0 ? 1u : 0u) | (gy == 0 || gy == n1 ? 2u : 0u) |
                     (gx >= 0 && gx <= n0 - 1 ? 4u : 0u) | (gx >= 0 && gx <= n0 ? 8u : 0u) |
                     (gy >= 0 && gy <= n1 - 1 ? 16u : 0u) | (gy >= 0 && gy <= n1 ? 32u : 0u) |
-                    (gx == 0 ? 64u : 0u) | (gy == 0 ? 128u : 0u);
+                    (gx == 0 ? 64u : 0u) | (gy == 0 ? 128u : 0u) | (past ? 256u : 0u);
             jrow[r] = reinterpret_cast<R*>(S.F) + (long long)comp_j(1 - par) * sc + (long long)(gy + G) * S.sy +
                       (gx + G);
         }
@@ -526,7 +531,7 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
                 for (int r = 0; r < NR; ++r) {
                     const int i = pidx[r];
                     if (i < 0) continue;
-                    if (doD && pout[r] >= 0) {
+                    if (doD && (pout[r] >= 0 || (pm[r] & 256u))) {
                         const R dNz_dy = N0[2 * BV + i + BX] - N0[2 * BV + i];
                         const R dNx_dy = N0[i + BX] - N0[i];
                         const R dNy_dz = N1[BV + i] - N0[BV + i];
@@ -546,10 +551,17 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
                             if (!(xs && ys && zn)) v[5] = R(0);
                         }
                         const int u = pout[r];
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) Out[c * TV + u] = v[c];
-                        // clear J_{1-p} on plane m (the next step deposits into it)
                         R* jp = jrow[r] + zoff;
+                        if (u >= 0) {
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) Out[c * TV + u] = v[c];
+                        } else {
+                            // past the tile (node plane x = n_x / y = n_y): plain stores
+                            R* ep = jp + (long long)(comp_eb(1 - par) - comp_j(1 - par)) * sc;
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) ep[c * sc] = v[c];
+                        }
+                        // clear J_{1-p} on plane m (the next step deposits into it)
                         jp[0] = R(0);
                         jp[sc] = R(0);
                         jp[2 * sc] = R(0);
