@@ -41,7 +41,7 @@ struct Group {
 
 // 3D field solver: columns of Y3_PX x Y3_PY points (x, y) marching along z through a
 // segment of planes; a ring of Y3_NS planes of E, B, J per column (TMA), Y3_NT threads.
-constexpr int Y3_PX = 32, Y3_PY = 8, Y3_NS = 4, Y3_NT = 416;
+constexpr int Y3_PX = 32, Y3_PY = 8, Y3_NS = 4, Y3_NT = 384;
 constexpr int Y3_BX = Y3_PX + 8, Y3_BY = Y3_PY + 4;
 // dynamic shared memory of the 3D field solver for element size es (bytes)
 __host__ __device__ constexpr size_t yee3_smem(int es)

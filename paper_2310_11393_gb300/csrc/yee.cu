@@ -353,8 +353,9 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
     constexpr size_t OOFF = NOFF + round128(6 * BV * sizeof(R));
     constexpr int AW = PX + 3, AH = PY + 3;      // Bh range: box x 2 .. PX+4, y 0 .. PY+2
     constexpr int NW = PX + 2, NH = PY + 2;      // N range:  box x 3 .. PX+4, y 1 .. PY+2
-    constexpr int NA = AW * AH;
-    constexpr int NR = (NA + NT - 1) / NT;       // Bh points per thread
+    constexpr int NE = 3 * PY + 8;               // Bh points off the core rows (see below)
+    constexpr int NR = 1;                        // Bh points per thread
+    static_assert(PX == 32 && NT == 32 * (AH + (NE + 31) / 32), "one warp per row of 32 points, plus the rest");
     static_assert((NS & (NS - 1)) == 0, "a ring of a power-of-two number of stages");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[NS];
@@ -369,19 +370,35 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
     R* Hr = reinterpret_cast<R*>(smem_raw + HOFF);     // [3][3][BY][BX]  Bh ring
     R* Nr = reinterpret_cast<R*>(smem_raw + NOFF);     // [2][3][BY][BX]  N ring
     R* Outb = reinterpret_cast<R*>(smem_raw + OOFF);   // [2][6][PY][PX]
-    // Every phase of a plane works on the thread's own points of the Bh range, a = tid + r NT
-    // (box x 2 + a % AW, y a / AW): Bh on all of them, N on those in the N range, the
-    // outputs (box x 4 .. PX+3, y 2 .. PY+1) on those in the tile.  Their box indices and
-    // output slots are fixed for the launch.
+    // Every phase of a plane works on the thread's own point of the Bh range: Bh on all of
+    // them, N on those in the N range, the outputs (box x 4 .. PX+3, y 2 .. PY+1) on those in
+    // the tile.  Warp w < AH holds row y = w, x = 4 .. 35 (32 consecutive box points: no bank
+    // conflicts in any phase); the last warp holds the rest of the range, x = 2 (y >= 1: Bh
+    // at (2, 0) feeds nothing), x = 3 and x = PX+4.  Box indices and output slots are fixed
+    // for the launch.
     int pidx[NR], pout[NR];
     bool pN[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const int a = tid + r * NT;
-        const int lx = 2 + a % AW, ly = a / AW;
-        pidx[r] = a < NA ? lx + BX * ly : -1;
-        pN[r] = a < NA && lx >= 3 && ly >= 1;
-        pout[r] = (a < NA && lx >= 4 && lx < PX + 4 && ly >= 2 && ly < PY + 2) ? (lx - 4) + PX * (ly - 2) : -1;
+    {
+        const int w = tid >> 5, lane = tid & 31;
+        int lx = 4 + lane, ly = w;
+        bool has = true;
+        if (w >= AH) {
+            const int e = lane + 32 * (w - AH);
+            has = e < NE;
+            if (e < PY + 2) {
+                lx = 2;
+                ly = 1 + e;
+            } else if (e < 2 * PY + 5) {
+                lx = 3;
+                ly = e - (PY + 2);
+            } else {
+                lx = PX + 4;
+                ly = e - (2 * PY + 5);
+            }
+        }
+        pidx[0] = has ? lx + BX * ly : -1;
+        pN[0] = has && lx >= 3 && ly >= 1;
+        pout[0] = (has && lx >= 4 && lx < PX + 4 && ly >= 2 && ly < PY + 2) ? (lx - 4) + PX * (ly - 2) : -1;
     }
     uint32_t ph = 0;      // mbarrier phase of each stage
     int oslot = 0;
@@ -419,8 +436,7 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
         R* jrow[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const int a = tid + r * NT;
-            const int gx = x0 - 4 + 2 + a % AW, gy = y0 - 2 + a / AW;
+            const int gx = x0 - 4 + pidx[r] % BX, gy = y0 - 2 + pidx[r] / BX;
             const bool past = (xend && gx == n0 && gy >= y0 && gy <= y0 + PY - (yend ? 0 : 1)) ||
                               (yend && gy == n1 && gx >= x0 && gx <= x0 + PX - (xend ? 0 : 1));
             pm[r] = (gx == 0 || gx == n0 ? 1u : 0u) | (gy == 0 || gy == n1 ? 2u : 0u) |
