@@ -290,11 +290,13 @@ Layout make_layout(const pic_config* c)
             L.yb[d] = d == 0 ? L.yt[d] + 8 : L.yt[d] + 4;
             L.yo[d] = L.yt[d];
             if (c->dim == 3 && d == 2) L.yb[d] = L.yo[d] = 1;     // one plane per load / store
-            long long need = N + 1 + 2 * G;
+            long long need = N + 1 + 2 * (d == 0 ? GX : G);
             if (d == 0) {
-                need = std::max<long long>(need, (long long)L.npt[d] * L.pt[d] + 8);
-                need = std::max<long long>(need, (long long)L.nyt[d] * L.yt[d] + 8);
-                need = (need + 3) / 4 * 4;
+                // boxes reach 4 points past the last tile; rows start on 128 bytes
+                need = std::max<long long>(need, (long long)L.npt[d] * L.pt[d] + 4 + GX);
+                need = std::max<long long>(need, (long long)L.nyt[d] * L.yt[d] + 4 + GX);
+                const int al = 128 / L.es;
+                need = (need + al - 1) / al * al;
             } else {
                 need = std::max<long long>(need, (long long)L.npt[d] * L.pt[d] + 7);
                 need = std::max<long long>(need, (long long)L.nyt[d] * L.yt[d] + 6);
@@ -1099,7 +1101,7 @@ pic_status pic_set_fields(pic_sim* s, const double* fields, void* stream)
                 if (!has) continue;
                 const double v = fields[comp * ne + ((long long)k * ext[1] + j) * ext[0] + i];
                 const long long o = comp * s->nalloc_tot + (long long)(D > 2 ? k + G : 0) * s->h.sz +
-                                    (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + G);
+                                    (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + GX);
                 if (s->es == 4) {
                     float f = (float)v;
                     memcpy(&buf[o * 4], &f, 4);
@@ -1270,7 +1272,7 @@ pic_status pic_diag(pic_sim* s, int kind, void* host_out, size_t bytes, void* st
                     double v = 0.0;
                     if (has) {
                         const long long idx = sc * s->nalloc_tot + (long long)(D > 2 ? k + G : 0) * s->h.sz +
-                                              (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + G);
+                                              (long long)(D > 1 ? j + G : 0) * s->h.sy + (i + GX);
                         if (es == 4) {
                             float f;
                             memcpy(&f, &src[idx * 4], 4);

@@ -79,7 +79,7 @@ __global__ void k_charge(const SimDev* __restrict__ sim, long long n, double* __
                 w[d][0] = 0.5 * (0.5 - dl) * (0.5 - dl);
                 w[d][1] = 0.75 - dl * dl;
                 w[d][2] = 0.5 * (0.5 + dl) * (0.5 + dl);
-                lo[d] = c[d] + h - 1 + G;
+                lo[d] = c[d] + h - 1 + (d == 0 ? GX : G);
             } else {
                 w[d][0] = 1.0;
                 w[d][1] = w[d][2] = 0.0;
@@ -110,7 +110,7 @@ __global__ void k_gauss(const SimDev* __restrict__ sim, const double* __restrict
         const int i = (int)(k % n0) + 1;
         const int j = D > 1 ? (int)((k / n0) % n1) + 1 : 0;
         const int l = D > 2 ? (int)(k / ((long long)n0 * n1)) + 1 : 0;
-        const long long o = (long long)(D > 2 ? l + G : 0) * S.sz + (long long)(D > 1 ? j + G : 0) * S.sy + (i + G);
+        const long long o = (long long)(D > 2 ? l + G : 0) * S.sz + (long long)(D > 1 ? j + G : 0) * S.sy + (i + GX);
         double div = ((double)F[eb + o] - (double)F[eb + o - 1]) * S.inv_dx;
         if (D > 1) div += ((double)F[eb + S.sc + o] - (double)F[eb + S.sc + o - S.sy]) * S.inv_dx;
         if (D > 2) div += ((double)F[eb + 2 * S.sc + o] - (double)F[eb + 2 * S.sc + o - S.sz]) * S.inv_dx;
@@ -137,7 +137,7 @@ __global__ void k_energy_fields(const SimDev* __restrict__ sim, int m0, int m1, 
          k += (long long)gridDim.x * blockDim.x) {
         const int g[3] = {(int)(k % m0), (int)((k / m0) % m1), (int)(k / ((long long)m0 * m1))};
         const long long o = (long long)(D > 2 ? g[2] + G : 0) * S.sz + (long long)(D > 1 ? g[1] + G : 0) * S.sy +
-                            (g[0] + G);
+                            (g[0] + GX);
         for (int comp = 0; comp < 6; ++comp) {
             const int c = comp % 3;
             bool has = true;

@@ -342,8 +342,8 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
         const int bxy = bx * by, bvol = bxy * bz;
         R* Fs = reinterpret_cast<R*>(smem_raw);   // [6][bz][by][bx]: Ex Ey Ez Bx By Bz at step n
         R* Js = reinterpret_cast<R*>(smem_raw + round128(6 * bvol * sizeof(R)));   // [3][bz][by][bx]
-        // box: x nodes [T0-4, T0+pt+4), y/z nodes [T0-2, T0+pt+3); array index = node + G
-        const int org[3] = {T0[0] - 4 + G, D > 1 ? T0[1] - 2 + G : 0, D > 2 ? T0[2] - 2 + G : 0};
+        // box: x nodes [T0-4, T0+pt+4), y/z nodes [T0-2, T0+pt+3); array index = node + GX (x), + G (y, z)
+        const int org[3] = {T0[0] - 4 + GX, D > 1 ? T0[1] - 2 + G : 0, D > 2 ? T0[2] - 2 + G : 0};
         if (tid == 0) {
             // the maps were written to device memory before the launch: one acquire per
             // simulation and block orders that write before this thread's TMA uses
@@ -1290,7 +1290,7 @@ __global__ void __launch_bounds__(256) k_incident_grid(const SimDev* __restrict_
     const PhaseRef<R> pr = s_pr;
     const BeamC<R>& bc = beam_of<R>(S);
     R* F = reinterpret_cast<R*>(S.F);
-    const long long base = (long long)(D > 2 ? z + G : 0) * S.sz + (long long)(D > 1 ? y + G : 0) * S.sy + (x + G);
+    const long long base = (long long)(D > 2 ? z + G : 0) * S.sz + (long long)(D > 1 ? y + G : 0) * S.sy + (x + GX);
     const long long eb = (long long)comp_eb(st->parity) * S.sc;
     const long long tb = (long long)COMP_TOTAL * S.sc;
     const int c[3] = {x, y, z};

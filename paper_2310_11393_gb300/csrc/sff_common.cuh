@@ -13,6 +13,9 @@ namespace sff {
 // Ghost points stored below (and at least this many above) every resolved axis.
 // Four keeps every TMA box start on the x axis a multiple of four elements.
 constexpr int G = 4;
+// ghost width along x: a multiple of 8, so that a tile starting on a multiple of 32 points
+// starts on a 32-byte sector (whole-sector stores of the field solver)
+constexpr int GX = 8;
 constexpr int NCOMP = 9;           // Ex Ey Ez Bx By Bz Jx Jy Jz
 constexpr unsigned DEAD = 0xFFFFFFFFu;
 constexpr int EXIT_DOUBLES = 6;    // u[3], w, id, step

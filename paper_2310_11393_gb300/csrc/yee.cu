@@ -103,7 +103,7 @@ __device__ __forceinline__ void yee_body(const SimDev* __restrict__ sims, const 
         const SimDev& S = ONE ? one : sims[w.sim];
         int l[3];
         tile_lo(S, w.tile, l);
-        const int o[3] = {l[0] - HX + G, D > 1 ? l[1] - HY + G : 0, D > 2 ? l[2] - HZ + G : 0};
+        const int o[3] = {l[0] - HX + GX, D > 1 ? l[1] - HY + G : 0, D > 2 ? l[2] - HZ + G : 0};
         const int p = S.st->parity;
         // one acquire per simulation and block (the maps were written before the launch)
         if (!ONE && w.sim != acq_sim) {
@@ -286,7 +286,7 @@ __device__ __forceinline__ void yee_body(const SimDev* __restrict__ sims, const 
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
-            const int oc[3] = {lo[0] + G, D > 1 ? lo[1] + G : 0, D > 2 ? lo[2] + G : 0};
+            const int oc[3] = {lo[0] + GX, D > 1 ? lo[1] + G : 0, D > 2 ? lo[2] + G : 0};
             tma_store_box<D>(&S.tm_yout, oc, comp_eb(1 - par), Out);
             bulk_commit();
         }
@@ -298,7 +298,7 @@ __device__ __forceinline__ void yee_body(const SimDev* __restrict__ sims, const 
                 const int c = k / TV, r = k - c * TV;
                 const int t0 = r % TX, t1 = (r / TX) % TY, t2 = r / (TX * TY);
                 Fg[jb + c * S.sc + (long long)(D > 2 ? lo[2] + t2 + G : 0) * S.sz +
-                   (long long)(D > 1 ? lo[1] + t1 + G : 0) * S.sy + (lo[0] + t0 + G)] = R(0);
+                   (long long)(D > 1 ? lo[1] + t1 + G : 0) * S.sy + (lo[0] + t0 + GX)] = R(0);
             }
         }
         if (tid == 0) bulk_wait_read0();
@@ -444,14 +444,14 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
                     (gy >= 0 && gy <= n1 - 1 ? 16u : 0u) | (gy >= 0 && gy <= n1 ? 32u : 0u) |
                     (gx == 0 ? 64u : 0u) | (gy == 0 ? 128u : 0u) | (past ? 256u : 0u);
             jrow[r] = reinterpret_cast<R*>(S.F) + (long long)comp_j(1 - par) * sc + (long long)(gy + G) * S.sy +
-                      (gx + G);
+                      (gx + GX);
         }
         auto stage_of = [&](int p) { return (p - pa) & (NS - 1); };
         auto Hs = [&](int p) { return Hr + ((p - pa) % 3) * 3 * BV; };
         auto Ns = [&](int p) { return Nr + ((p - pa) & 1) * 3 * BV; };
         auto issue = [&](int p) {
             const int sgi = stage_of(p);
-            const int org[3] = {x0 - 4 + G, y0 - 2 + G, p + G};
+            const int org[3] = {x0 - 4 + GX, y0 - 2 + G, p + G};
             mbar_arrive_expect_tx(&bars[sgi], (unsigned)(9 * BV * sizeof(R)));
             tma_load_box<3>(In(sgi), &S.tm_yin, org, comp_eb(par), &bars[sgi]);
             tma_load_box<3>(reinterpret_cast<unsigned char*>(In(sgi)) + JOFF, &S.tm_yj, org, comp_j(par), &bars[sgi]);
@@ -602,7 +602,7 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
             }
             if (doD) {
                 if (tid == 0) {
-                    const int oc[3] = {x0 + G, y0 + G, q - 1 + G};
+                    const int oc[3] = {x0 + GX, y0 + G, q - 1 + G};
                     tma_store_box<3>(&S.tm_yout, oc, comp_eb(1 - par), Outb + oslot * 6 * TV);
                     bulk_commit();
                 }
