@@ -8,8 +8,10 @@ Default workload: the largest single-GPU configuration, the 3D tightly focused R
 256 x 128 x 128-cell slab at 0.01 n_c with 4 ppc = 16 777 216 electrons).  The K timed steps
 are the window of the run centred on the step at which the pulse peak crosses the focus
 (the simulation is first advanced to the window's start, untimed); --window start times
-the first K steps instead.  Metric: particle-pushes/s (each push includes the
-incident-field evaluation and the deposit).
+the first K steps instead; without --steps the whole run is timed.  Metric:
+particle-pushes/s (each push includes the incident-field evaluation and the deposit),
+counted exactly: an electron alive at the end counts every timed step, one that left the
+box counts the timed steps up to the one in which it left (its exit record).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 3d|2d|1d]
 
@@ -50,6 +52,8 @@ def parse():
     ap.add_argument("--window", default="focus", choices=["focus", "start"],
                     help="timed steps centred on the pulse crossing the focus (default) or from t = 0")
     ap.add_argument("--scale", type=int, default=1, help="1d/2d/3d: box divided by this per axis (profiling)")
+    ap.add_argument("--slab-cells", type=int, default=0,
+                    help="1d/2d/3d: electron slab cut to this many cells per axis (profiling the field solve)")
     ap.add_argument("--tile", default="", help="particle tile, e.g. 16,8,4 (skips the autotuner's tile search)")
     ap.add_argument("--chunk", type=int, default=0, help="particles per push work item (skips its autotuning)")
     ap.add_argument("--autotune", type=int, default=10,
@@ -69,6 +73,7 @@ def parse():
 
 SCALE = 1
 INCIDENT_GRID = 0
+SLAB_CELLS = 0
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from the
 # ncu capture summarised in profiles/ (kept in step with the kernel: set to None when the
@@ -86,6 +91,11 @@ PROFILED_TRAFFIC = {
 def workload(name):
     w = {"1d": synth.c1_1d_plane, "2d": synth.c2_2d_lp, "3d": synth.c3_3d_rp, "2d_gauss": synth.c6_2d_gauss}[name]()
     w = w if SCALE == 1 else synth.scaled(w, SCALE)
+    if SLAB_CELLS > 0:
+        # profiling: the electron slab cut to SLAB_CELLS cells per axis at its low corner
+        # (the grid and the field solve unchanged, the device state a few GB)
+        hi = tuple(min(w.slab_hi[d], w.slab_lo[d] + SLAB_CELLS) if d < w.dim else w.slab_hi[d] for d in range(3))
+        w = w.with_(slab_hi=hi, name=w.name + f"_slab{SLAB_CELLS}")
     return w.with_(incident_grid=INCIDENT_GRID, name=w.name + ("_incgrid" if INCIDENT_GRID else ""))
 
 
@@ -188,6 +198,14 @@ def shard(n, rank, world):
     return list(range(rank, n, world))
 
 
+def pushes_of(sim, s0, steps, n_end):
+    """Pushes in the steps s0 .. s0+steps-1: every electron alive at the end was pushed in
+    each of them, and one that left the box in step e (its exit record) in steps s0 .. e."""
+    ex = sim.exits()["step"]
+    ex = ex[(ex >= s0) & (ex < s0 + steps)]
+    return float(n_end) * steps + float(np.sum(ex - s0 + 1))
+
+
 def job_totals(pushes, secs, world, device=None):
     """Whole-job pushes (sum over ranks) and time (max over ranks)."""
     if world <= 1:
@@ -253,7 +271,6 @@ def run_ours(args, rank, world, local_rank):
     if s0:
         sim.step(s0)
     torch.cuda.synchronize()
-    n_a = sim.info().n_alive
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -271,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     n_b = sim.info().n_alive
-    pushes = 0.5 * (n_a + n_b) * args.steps
+    pushes = pushes_of(sim, s0, args.steps, n_b)
     tot_pushes, t_max = job_totals(pushes, secs, world, dev)
     info = sim.info()
     sim.close()
@@ -382,8 +399,8 @@ def run_e2e(args, w, cfg, pic, torch, stream, alloc, snap, s0):
     t1 = time.perf_counter()
     n_end = len(out["id"])
     d2h = n_end * rec + 64
+    pushes = pushes_of(sim, s0, args.steps, n_end)
     sim.close()
-    pushes = 0.5 * (n + n_end) * args.steps
     return {"value": pushes / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d / args.steps),
             "d2h_bytes_per_step": int(d2h / args.steps), "seconds": t1 - t0,
             "what": f"restore the state at step {s0} from host arrays (particles, E and B), {args.steps} steps, "
@@ -420,12 +437,14 @@ def _oracle_worker(job):
     sim = oracle.Sim(oracle.config_from(w))
     if warm:
         sim.step(warm)
-    n0 = sim.num_particles()
     t0 = time.perf_counter()
     sim.step(steps)
     t1 = time.perf_counter()
-    n1 = sim.num_particles()
-    return 0.5 * (n0 + n1) * steps, t1 - t0
+    # counted like the device runs: the electrons alive at the end every step, the ones that
+    # left in steps warm .. e
+    ex = sim.exits()["step"]
+    ex = ex[ex >= warm]
+    return float(sim.num_particles()) * steps + float(np.sum(ex - warm + 1)), t1 - t0
 
 
 def oracle_all_cores(w, warm, steps):
@@ -702,8 +721,9 @@ def main():
     args = parse()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(relaunch_ranks(args))
-    global SCALE, INCIDENT_GRID
+    global SCALE, INCIDENT_GRID, SLAB_CELLS
     SCALE = max(1, args.scale)
+    SLAB_CELLS = max(0, args.slab_cells)
     INCIDENT_GRID = 1 if args.incident == "grid" else 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
