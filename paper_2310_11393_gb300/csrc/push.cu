@@ -411,9 +411,13 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
                 R o[3] = {R(0), R(0), R(0)};
 #pragma unroll
                 for (int d = 0; d < D; ++d) o[d] = reinterpret_cast<const R*>(S.off[par][d])[p];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) u[d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
-                wt = reinterpret_cast<const R*>(S.wgt[par])[p];
+
+                // ---- incident field at (x^n, t^n) (in a total-field run, or when it was
+                // evaluated on the grid, it is in the gathered field already).  Evaluated
+                // before the gather, and the momentum and weight loaded after it: fewer values
+                // live across the closed form, the most register-hungry part of the push ----
+                R Ei[3] = {R(0), R(0), R(0)}, Bi[3] = {R(0), R(0), R(0)};
+                if (!S.tf && !S.incgrid) incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
 
                 // ---- gather of the scattered field (order-2 shapes on the Yee stagger) ----
                 R Wp[3][3], Wd[3][3];
@@ -431,25 +435,16 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
                         Wp[d][1] = Wd[d][1] = Wp[d][2] = Wd[d][2] = R(0);
                     }
                 }
-                R E[3], B[3];
-                E[0] = interp<D, R>(Fs + 0 * bvol, bx, bxy, ld[0], lp[1], lp[2], Wd[0], Wp[1], Wp[2]);
-                E[1] = interp<D, R>(Fs + 1 * bvol, bx, bxy, lp[0], ld[1], lp[2], Wp[0], Wd[1], Wp[2]);
-                E[2] = interp<D, R>(Fs + 2 * bvol, bx, bxy, lp[0], lp[1], ld[2], Wp[0], Wp[1], Wd[2]);
-                B[0] = interp<D, R>(Fs + 3 * bvol, bx, bxy, lp[0], ld[1], ld[2], Wp[0], Wd[1], Wd[2]);
-                B[1] = interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
-                B[2] = interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
-
-                // ---- incident field at (x^n, t^n) (in a total-field run, or when it was
-                // evaluated on the grid, it is in the gathered field already) ----
-                if (!S.tf && !S.incgrid) {
-                    R Ei[3], Bi[3];
-                    incident_at<D, R>(S, bc, pref, c, o, Ei, Bi);
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        E[d] += Ei[d];
-                        B[d] += Bi[d];
-                    }
-                }
+                for (int d = 0; d < 3; ++d) u[d] = reinterpret_cast<const R*>(S.mom[par][d])[p];
+                wt = reinterpret_cast<const R*>(S.wgt[par])[p];
+                R E[3], B[3];
+                E[0] = Ei[0] + interp<D, R>(Fs + 0 * bvol, bx, bxy, ld[0], lp[1], lp[2], Wd[0], Wp[1], Wp[2]);
+                E[1] = Ei[1] + interp<D, R>(Fs + 1 * bvol, bx, bxy, lp[0], ld[1], lp[2], Wp[0], Wd[1], Wp[2]);
+                E[2] = Ei[2] + interp<D, R>(Fs + 2 * bvol, bx, bxy, lp[0], lp[1], ld[2], Wp[0], Wp[1], Wd[2]);
+                B[0] = Bi[0] + interp<D, R>(Fs + 3 * bvol, bx, bxy, lp[0], ld[1], ld[2], Wp[0], Wd[1], Wd[2]);
+                B[1] = Bi[1] + interp<D, R>(Fs + 4 * bvol, bx, bxy, ld[0], lp[1], ld[2], Wd[0], Wp[1], Wd[2]);
+                B[2] = Bi[2] + interp<D, R>(Fs + 5 * bvol, bx, bxy, ld[0], ld[1], lp[2], Wd[0], Wd[1], Wp[2]);
 
                 // ---- momentum update, charge -1, mass 1 (u^{n-1/2} -> u^{n+1/2}) ----
                 if (S.pusher == 1) vay_update<R>(u, E, B, hq);
