@@ -372,7 +372,7 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
         }
 
         const BeamC<R>& bc = beam_of<R>(S);
-        const PhaseRef<R> pref = s_pref;
+        const PhaseRef<R>& pref = s_pref;     // read from shared memory where used (no registers held)
         // fixed-point scale of this item's current (FP32; unused in FP64)
         const float wmax = st->wmax;
         const R jq = (sizeof(R) == 4 && wmax > 0.f) ? R(JQ_RANGE / ((float)max(p1 - p0, 256) * wmax)) : R(0);
@@ -489,6 +489,63 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
                     }
                     jw[d] = c[d] + h0 - (lo ? 2 : 1) - T0[d] + hx[d];
                 }
+                // ---- move: carry the offset into the cell index; removal near the faces.
+                // Done before the deposit's loops below, so that across them only the new cell,
+                // offsets and destination stay live (not the old cell, offsets and move) ----
+                int cn[3] = {c[0], c[1], c[2]};
+                bool dead = false;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const R x = o[d] + mv[d];
+                    const R fl = m_floor(x);
+                    R r = x - fl;
+                    int k = (int)fl;
+                    if (r >= R(1)) {
+                        r -= R(1);
+                        k += 1;
+                    }
+                    cn[d] = c[d] + k;
+                    on[d] = r;
+                    if (cn[d] < S.margin || cn[d] >= S.n[d] - S.margin) dead = true;
+                }
+                if (dead) {
+                    const int slot = atomicAdd(&st->n_exits, 1);
+                    if (slot < S.max_exits) {
+                        double* e = S.exits + (long long)slot * EXIT_DOUBLES;
+                        e[0] = (double)u[0];
+                        e[1] = (double)u[1];
+                        e[2] = (double)u[2];
+                        e[3] = (double)wt;
+                        e[4] = (double)S.pid[par][p];
+                        e[5] = (double)st->step;
+                    } else {
+                        atomicOr(&st->status, (unsigned)FLAG_EXIT_OVERFLOW);
+                    }
+                } else {
+                    // destination tile relative to this one (a move is under one cell per axis)
+                    int hidx = 0, mul = 1, tg = 0, tmul = 1;
+                    int rel[3] = {0, 0, 0};
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        rel[d] = cn[d] < T0[d] ? -1 : (cn[d] >= T0[d] + S.pt[d] ? 1 : 0);
+                        hidx += (rel[d] + 1) * mul;
+                        mul *= 3;
+                        tg += (tc[d] + rel[d]) * tmul;
+                        tmul *= S.npt[d];
+                    }
+                    atomicAdd(&s_hist[hidx], 1);
+                    frame_count<D>(S, cn, T0, rel, s_frame);
+                    ncl = encode_cell<D>(S, cn);
+                    tdst = tg;
+                }
+                if (!direct) {
+                    S.cell[par][p] = ncl;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
+                }
+                // ---- the deposit on the windows set up above ----
                 // window width per axis over the lanes running here (each lane's own vote is in
                 // its mask, so its width covers its own window whatever the warp's convergence)
                 const unsigned am = __activemask();
@@ -606,60 +663,6 @@ __device__ __forceinline__ void push_body(const SimDev* __restrict__ sims, const
                     }
                 }
 
-                // ---- move: carry the offset into the cell index; removal near the faces ----
-                int cn[3] = {c[0], c[1], c[2]};
-                bool dead = false;
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const R x = o[d] + mv[d];
-                    const R fl = m_floor(x);
-                    R r = x - fl;
-                    int k = (int)fl;
-                    if (r >= R(1)) {
-                        r -= R(1);
-                        k += 1;
-                    }
-                    cn[d] = c[d] + k;
-                    on[d] = r;
-                    if (cn[d] < S.margin || cn[d] >= S.n[d] - S.margin) dead = true;
-                }
-                if (dead) {
-                    const int slot = atomicAdd(&st->n_exits, 1);
-                    if (slot < S.max_exits) {
-                        double* e = S.exits + (long long)slot * EXIT_DOUBLES;
-                        e[0] = (double)u[0];
-                        e[1] = (double)u[1];
-                        e[2] = (double)u[2];
-                        e[3] = (double)wt;
-                        e[4] = (double)S.pid[par][p];
-                        e[5] = (double)st->step;
-                    } else {
-                        atomicOr(&st->status, (unsigned)FLAG_EXIT_OVERFLOW);
-                    }
-                } else {
-                    // destination tile relative to this one (a move is under one cell per axis)
-                    int hidx = 0, mul = 1, tg = 0, tmul = 1;
-                    int rel[3] = {0, 0, 0};
-#pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        rel[d] = cn[d] < T0[d] ? -1 : (cn[d] >= T0[d] + S.pt[d] ? 1 : 0);
-                        hidx += (rel[d] + 1) * mul;
-                        mul *= 3;
-                        tg += (tc[d] + rel[d]) * tmul;
-                        tmul *= S.npt[d];
-                    }
-                    atomicAdd(&s_hist[hidx], 1);
-                    frame_count<D>(S, cn, T0, rel, s_frame);
-                    ncl = encode_cell<D>(S, cn);
-                    tdst = tg;
-                }
-                if (!direct) {
-                    S.cell[par][p] = ncl;
-#pragma unroll
-                    for (int d = 0; d < D; ++d) reinterpret_cast<R*>(S.off[par][d])[p] = on[d];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) reinterpret_cast<R*>(S.mom[par][d])[p] = u[d];
-                }
             }
             // ---- placement into the destination tile's slots of the other buffer set (all
             // lanes of the warp take part in the reservation) ----
