@@ -79,11 +79,11 @@ SLAB_CELLS = 0
 # ncu capture summarised in profiles/ (kept in step with the kernel: set to None when the
 # kernel changes and until it is captured again)
 PROFILED_TRAFFIC = {
-    ("2d_lp_1024sq", "k_push1<2,float>"): (111.2e6, "profiles/k_push_2d_lp_1024sq.md, step 762 (focus)"),
+    ("2d_lp_1024sq", "k_push1<2,float>"): (108.4e6, "profiles/k_push_2d_lp_1024sq.md, step 762 (focus)"),
     # the full 3D state (14 GB) is too large for a multi-pass capture: the box halved per axis
     # (2.1 M electrons, step 233 at the focus), scaled by the electrons (x8): the push's traffic
     # is per particle (record read and written) plus the grid per cell, both x8
-    ("3d_rp_512x256x256", "k_push1<3,float>"): (8 * 166.6e6, "profiles/k_push_3d_rp_256x128x128.md, box halved per "
+    ("3d_rp_512x256x256", "k_push1<3,float>"): (8 * 161.3e6, "profiles/k_push_3d_rp_256x128x128.md, box halved per "
                                                              "axis at the focus, scaled x8 by electrons and cells"),
 }
 
