@@ -331,10 +331,13 @@ __global__ void __launch_bounds__(256) k_yee1(const __grid_constant__ SimDev one
 // The column marches along z; plane k of E, B and J_p (box x: 4 points of halo on each
 // side, y: 2 below and 1 above) arrives by TMA into a ring of NS stages.  With
 //   A(k): Bh = B^{n+1/2} on plane k     (forward differences; planes k, k+1)
-//   B(k): N  = E^{n+1}   on plane k     (backward differences; Bh of planes k, k-1),
-//         then the Mur faces of plane k (plane 0: once N(1) exists)
+//   B(k): N  = E^{n+1}   on plane k     (backward differences; Bh of planes k, k-1), the
+//         Mur condition on its x / y faces from the inward neighbour's E^{n+1} evaluated
+//         by the face point's own thread; on the z faces (planes 0, n_z) separate passes
+//         (plane 0 once N(1) exists)
 //   D(k): B^{n+1} on plane k from Bh(k), N(k), N(k+1); E^{n+1}, B^{n+1} of plane k leave
-//         by one TMA store (double-buffered) and J_{1-p} of plane k is cleared,
+//         by one TMA store (double-buffered) and J_{1-p} of plane k is cleared; a column
+//         that ends at x = n_x (y = n_y) also writes that node plane with plain stores,
 // iteration q runs A(q+1) together with D(q-1), then B(q+1): two barriers per plane.
 // Bh is kept for x in [x0-2, x0+PX], y in [y0-2, y0+PY]; N for x in [x0-1, x0+PX],
 // y in [y0-1, y0+PY] and planes from z0-1: one more than the outputs need on the low
@@ -351,7 +354,7 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
     constexpr size_t HOFF = NS * STAGE;
     constexpr size_t NOFF = HOFF + round128(9 * BV * sizeof(R));
     constexpr size_t OOFF = NOFF + round128(6 * BV * sizeof(R));
-    constexpr int AW = PX + 3, AH = PY + 3;      // Bh range: box x 2 .. PX+4, y 0 .. PY+2
+    constexpr int AH = PY + 3;                   // Bh range: box x 2 .. PX+4, y 0 .. PY+2
     constexpr int NW = PX + 2, NH = PY + 2;      // N range:  box x 3 .. PX+4, y 1 .. PY+2
     constexpr int NE = 3 * PY + 8;               // Bh points off the core rows (see below)
     constexpr int NR = 1;                        // Bh points per thread
