@@ -1,6 +1,7 @@
 """Field solver alone: white-noise E, B in an empty box (no particles, so J = 0) advanced by
 the CUDA path and by the oracle.  Every point of every component, the Mur faces, edges and
-corners included, and (3D) columns both away from and on the faces of the box."""
+corners included, and (3D) columns both away from and on the faces of the box, and columns
+that end on the node planes x = n_x, y = n_y (which they write for the absent next column)."""
 import numpy as np
 import pytest
 
@@ -10,6 +11,9 @@ from _support import small_1d, small_2d, small_3d
 pytestmark = pytest.mark.gpu
 
 SHAPES = {1: (300, 1, 1), 2: (100, 70, 1), 3: (80, 40, 48)}
+# 3D: x a multiple of the 32-point column and y of its 8 rows, so that the node planes
+# x = n_x and y = n_y (and their edge) are written by the columns that end on them
+SHAPE_3D_ENDS = (64, 40, 33)
 
 
 @pytest.fixture(scope="module")
@@ -42,14 +46,15 @@ def noise_fields(n, dim, seed):
     return F
 
 
-@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("dim,shape", [(1, SHAPES[1]), (2, SHAPES[2]), (3, SHAPES[3]), (3, SHAPE_3D_ENDS)],
+                         ids=["1d", "2d", "3d", "3d_node_planes"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_vacuum_field_solve_matches_oracle(P, orc, dim, prec):
+def test_vacuum_field_solve_matches_oracle(P, orc, dim, shape, prec):
     make = {1: small_1d, 2: small_2d, 3: small_3d}[dim]
-    w = make().with_(n=SHAPES[dim], ppc=0, precision=synth.FP32 if prec == "fp32" else synth.FP64)
+    w = make().with_(n=shape, ppc=0, precision=synth.FP32 if prec == "fp32" else synth.FP64)
     sim = P.Simulation(P.config_from(w))
     ref = orc.Sim(orc.config_from(w))
-    F = noise_fields(SHAPES[dim], dim, seed=40 + dim)
+    F = noise_fields(shape, dim, seed=40 + dim)
     sim.set_fields(F)
     ref.set_fields(F)
     tol = 1e-5 if prec == "fp32" else 1e-12
