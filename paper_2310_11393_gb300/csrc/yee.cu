@@ -524,6 +524,10 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
 
         bool failed = false;
         for (int q = z0 - 3; q <= z1; ++q) {
+            // Plane q was last read in the previous iteration unless this one's z-face passes
+            // read it (B(n_z) reads E(n_z - 1), the plane-0 faces E(0)): otherwise its stage
+            // takes plane q+NS as soon as this iteration's first barrier has passed
+            const bool early = q + 1 != n2 && q + 1 != 1;
             bool ok = true;
             while (pw < min(q + 2, plast)) {
                 ++pw;
@@ -602,6 +606,10 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
+            }
+            if (early && q >= pa && q + NS <= plast) {
+                if (tid == 0) issue(q + NS);
+                pissued = q + NS;
             }
             if (doD) {
                 if (tid == 0) {
@@ -685,8 +693,8 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
                 if (tid == 0) bulk_wait_read1();
                 __syncthreads();
             }
-            // plane q is no longer read: its stage takes plane q+NS
-            if (q >= pa && q + NS <= plast) {
+            // (z faces) plane q is no longer read: its stage takes plane q+NS
+            if (!early && q >= pa && q + NS <= plast) {
                 if (tid == 0) issue(q + NS);
                 pissued = q + NS;
             }
