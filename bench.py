@@ -299,7 +299,9 @@ def run_ours(args, rank, world, local_rank):
         psim.step(s0)
     snap = None
     if not args.no_e2e:      # the state at the window's start, for the end-to-end run
-        snap = (psim.particles(), psim.fields())
+        # held as a user keeps a checkpoint: one contiguous host array per quantity
+        parts = {k: np.ascontiguousarray(v) for k, v in psim.particles().items()}
+        snap = (parts, np.ascontiguousarray(psim.fields()))
     nsteps_prof = args.steps if args.profile_steps <= 0 else min(args.steps, args.profile_steps)
     nwin = 10 if nsteps_prof >= 10 else 1
     prof = np.zeros(5)

@@ -981,10 +981,13 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
     // converted on several host threads; each range reports its first invalid particle
     const int nb = 16;
     std::vector<long long> bad(nb, -1);
-    std::atomic<int> slot{0};
+    std::vector<double> wmx(nb, 0.0);       // largest |weight| of each range
+    std::atomic<int> slot{0}, wslot{0};
     host_parallel(n, 1 << 16, [&](long long p0, long long p1) {
         long long first = -1;
+        double wm_r = 0.0;
         for (long long p = p0; p < p1 && first < 0; ++p) {
+            wm_r = std::max(wm_r, std::fabs(w[p]));
             int c[3] = {0, 0, 0};
             for (int d = 0; d < D; ++d) {
                 const double X = x[3 * p + d] / s->cfg.dx;
@@ -1025,6 +1028,8 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
             const int k = slot.fetch_add(1);
             if (k < nb) bad[k] = first;
         }
+        const int kw = wslot.fetch_add(1);
+        if (kw < nb) wmx[kw] = wm_r;
     });
     long long first_bad = -1;
     for (long long b : bad)
@@ -1066,7 +1071,7 @@ pic_status pic_set_particles(pic_sim* s, int64_t n, const double* x, const doubl
     {
         // largest |weight| (rounded up in FP32): the scale of the FP32 push's fixed-point current
         double wm = 0.0;
-        for (long long p = 0; p < n; ++p) wm = std::max(wm, std::fabs(w[p]));
+        for (double v : wmx) wm = std::max(wm, v);
         ds.wmax = wm > 0 ? std::nextafter((float)wm, INFINITY) : 0.f;
         if ((r = write_state(s, ds, st)) != PIC_OK) return r;
     }
@@ -1084,7 +1089,14 @@ pic_status pic_set_fields(pic_sim* s, const double* fields, void* stream)
     const int D = s->cfg.dim;
     const int ext[3] = {s->h.n[0] + 1, D > 1 ? s->h.n[1] + 1 : 1, D > 2 ? s->h.n[2] + 1 : 1};
     const long long ne = (long long)ext[0] * ext[1] * ext[2];
-    std::vector<char> buf((size_t)6 * s->nalloc_tot * s->es, 0);
+    // the device layout of E, B (zero at the points a component does not have and in the
+    // ghost region), zero-filled on several host threads
+    const size_t nbuf = (size_t)6 * s->nalloc_tot * s->es;
+    std::unique_ptr<char[]> buf(new char[nbuf]);
+    host_parallel((long long)((nbuf + 4095) / 4096), 1 << 10, [&](long long b0, long long b1) {
+        const size_t a = (size_t)b0 * 4096, e = std::min(nbuf, (size_t)b1 * 4096);
+        memset(buf.get() + a, 0, e - a);
+    });
     // rows (comp, k, j) of the host array converted on up to 16 host threads
     const long long nrows = 6LL * ext[2] * ext[1];
     host_parallel(nrows, 256, [&](long long r0, long long r1) {
@@ -1112,7 +1124,7 @@ pic_status pic_set_fields(pic_sim* s, const double* fields, void* stream)
         }
     });
     char* F = (char*)s->h.F;
-    CU_CHECK(s, cudaMemcpyAsync(F + (size_t)comp_eb(ds.parity) * s->nalloc_tot * s->es, buf.data(), buf.size(),
+    CU_CHECK(s, cudaMemcpyAsync(F + (size_t)comp_eb(ds.parity) * s->nalloc_tot * s->es, buf.get(), nbuf,
                                 cudaMemcpyHostToDevice, st));
     CU_CHECK(s, cudaStreamSynchronize(st));
     return PIC_OK;

@@ -420,13 +420,13 @@ class Simulation:
 
     def particles(self):
         n = self.info().n_alive
-        out = np.zeros((n, 8))
+        out = np.empty((n, 8))          # every entry is written
         pic_diag(self.h, PIC_DIAG_PARTICLES, out, self.stream)
         return {"x": out[:, 0:3], "u": out[:, 3:6], "w": out[:, 6], "id": out[:, 7].astype(np.int64)}
 
     def exits(self):
         n = self.info().n_exits
-        out = np.zeros((n, 6))
+        out = np.empty((n, 6))          # every entry is written
         pic_diag(self.h, PIC_DIAG_EXITS, out, self.stream)
         return {"u": out[:, 0:3], "w": out[:, 3], "id": out[:, 4].astype(np.int64), "step": out[:, 5].astype(np.int64)}
 
