@@ -256,7 +256,7 @@ void choose_tiles(const pic_config* c, int pt[3], int yt[3])
     if (c->dim == 1) {
         pt[0] = 32; yt[0] = 128;
     } else if (c->dim == 2) {
-        pt[0] = 16; pt[1] = 16; yt[0] = 32; yt[1] = 16;
+        pt[0] = 16; pt[1] = 16; yt[0] = Y2_PX; yt[1] = Y2_PY;
     } else {
         // columns of Y3_PX x Y3_PY marching along z in segments: at least ~600 work items
         // (a few per resident block on a full GPU), segments of at most 64 planes
@@ -338,8 +338,9 @@ Layout make_layout(const pic_config* c)
     const long long ytv = (long long)L.yt[0] * L.yt[1] * L.yt[2];
     L.push_smem = round128((size_t)(6 * pbv * L.es)) + (size_t)(3 * pbv * L.es);
     L.yee_smem = c->dim == 3 ? yee3_smem(L.es)
-                             : 2 * round128(round128((size_t)(6 * ybv * L.es)) + (size_t)(3 * ybv * L.es)) +
-                                   (size_t)(6 * ytv * L.es);      // two box buffers + the output tile
+                 : c->dim == 2 ? yee2_smem(L.es)
+                               : 2 * round128(round128((size_t)(6 * ybv * L.es)) + (size_t)(3 * ybv * L.es)) +
+                                     (size_t)(6 * ytv * L.es);      // two box buffers + the output tile
     size_t b = 0;
     b += align256(sizeof(SimDev)) + align256(sizeof(DevState));
     b += align256((size_t)L.ncomp * L.natot * L.es);

@@ -43,6 +43,15 @@ struct Group {
 // segment of planes; a ring of Y3_NS planes of E, B, J per column (TMA), Y3_NT threads.
 constexpr int Y3_PX = 32, Y3_PY = 8, Y3_NS = 4, Y3_NT = 384;
 constexpr int Y3_BX = Y3_PX + 8, Y3_BY = Y3_PY + 4;
+// 2D field solver: tiles of 32 x Y2_PY points, one warp per box row plus the rest
+constexpr int Y2_PX = 32, Y2_PY = 16;
+constexpr int Y2_NT = 32 * ((Y2_PY + 3) + (3 * Y2_PY + 8 + 31) / 32);
+// dynamic shared memory of the 2D field solver: two box buffers, Bh, N, the output tile
+__host__ __device__ constexpr size_t yee2_smem(int es)
+{
+    return 2 * round128(round128(6ull * (Y2_PX + 8) * (Y2_PY + 4) * es) + 3ull * (Y2_PX + 8) * (Y2_PY + 4) * es) +
+           2 * round128(3ull * (Y2_PX + 8) * (Y2_PY + 4) * es) + 6ull * Y2_PX * Y2_PY * es;
+}
 // dynamic shared memory of the 3D field solver for element size es (bytes)
 __host__ __device__ constexpr size_t yee3_smem(int es)
 {
@@ -93,12 +102,12 @@ void launch_eval_incident(const SimDev* sim, int dim, int prec, long long n, con
 // streaming multiprocessors of the current device (queried once per device)
 int device_sms();
 
-// Is field-solver tile t a work item?  In 3D a column whose first point lies on the node
-// plane x = n_x (or y = n_y), which holds nothing else, is not: the column before it writes
-// that plane of E and B and clears its J.
+// Is field-solver tile t a work item?  In 2D and 3D a tile (column) whose first point lies on
+// the node line / plane x = n_x (or y = n_y), which holds nothing else, is not: the one before
+// it writes that line / plane of E and B and clears its J.
 inline bool yee_tile_active(const SimDev& h, int dim, int t)
 {
-    if (dim != 3) return true;
+    if (dim == 1) return true;
     const int cx = t % h.nyt[0], cy = (t / h.nyt[0]) % h.nyt[1];
     return cx * h.yt[0] != h.n[0] && cy * h.yt[1] != h.n[1];
 }

@@ -1,6 +1,7 @@
-// Field solver of the scattered field (Eqs. MAmper, MFaraday; Yee stagger), sm_103a.
+// Field solver of the scattered field (Eqs. MAmper, MFaraday; Yee stagger), sm_103a:
+// `k_yee` (1D), `k_yee2r` (2D tiles, below) and `k_yee3s` (3D columns streamed along z).
 //
-// One work item = one tile of TX x TY x TZ points (compile-time shape).  The tile's box
+// 1D: one work item = one tile of TX x TY x TZ points (compile-time shape).  The tile's box
 // (x: 4 points of halo on each side, y/z: 2) of E, B at step n (buffer set p) and of
 // J^{n+1/2} (J_p) arrives by two TMA loads.  In shared memory:
 //   A. B^{n+1/2} = B^n - (dt/2) curl E^n             (forward differences, in place)
@@ -324,6 +325,249 @@ __global__ void __launch_bounds__(256) k_yee1(const __grid_constant__ SimDev one
                                               int nwork, int* __restrict__ counter)
 {
     yee_body<D, R, TX, TY, TZ, true>(nullptr, one, work, nwork, counter);
+}
+
+// ---------------------------------------------------------------------------------
+// 2D: one tile of PX x PY points per work item; its box (x: 4 points of halo on each side,
+// y: 2 below and 2 above) of E, B and J_p arrives by two TMA loads into one of two
+// buffers (the next tile's loads are in flight while this one is updated).  Phases, each
+// on the thread's own point of the box (fixed for the launch):
+//   A: Bh = B^{n+1/2}  for x in [x0-2, x0+PX], y in [y0-2, y0+PY]   (forward differences)
+//   B: N  = E^{n+1}    for x in [x0-1, x0+PX], y in [y0-1, y0+PY]   (backward differences),
+//      with the first-order Mur condition on the x / y faces evaluated from the inward
+//      neighbour's E^{n+1} by the face point's own thread (for E_z on a corner, the
+//      neighbour's neighbour too), so no extra passes or barriers
+//   D: B^{n+1} on the tile from Bh and N (forward differences); E^{n+1}, B^{n+1} leave by
+//      one TMA store and J_{1-p} is cleared; a tile that ends at x = n_x (y = n_y) also
+//      writes that node line with plain stores (no work item holds only the node line).
+// Warp w < AH holds box row w, x = 4 .. PX+3 (32 consecutive words: no bank conflicts);
+// the last warps hold the rest of the Bh range (x = 2, 3 and PX+4).
+// ---------------------------------------------------------------------------------
+template <typename R, int PY, int NT, bool ONE>
+__device__ __forceinline__ void yee2r_body(const SimDev* __restrict__ sims, const SimDev& one,
+                                           const Work* __restrict__ work, int nwork, int* __restrict__ counter)
+{
+    constexpr int PX = 32;
+    constexpr int BX = PX + 8, BY = PY + 4, BV = BX * BY, TV = PX * PY;
+    constexpr size_t JOFF = round128(6 * BV * sizeof(R));
+    constexpr size_t BOXB = round128(JOFF + 3 * BV * sizeof(R));   // one box buffer
+    constexpr size_t HOFF = 2 * BOXB;                              // Bh [3][BV]
+    constexpr size_t NOFF = HOFF + round128(3 * BV * sizeof(R));   // N  [3][BV]
+    constexpr size_t OOFF = NOFF + round128(3 * BV * sizeof(R));   // Out [6][PY][PX]
+    constexpr int AH = PY + 3;                   // Bh rows 0 .. PY+2
+    constexpr int NE = 3 * PY + 8;               // Bh points off the core rows
+    static_assert(NT == 32 * (AH + (NE + 31) / 32), "one warp per row of 32 points, plus the rest");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phases = 0;     // mbarrier phase per buffer
+    R* Hb = reinterpret_cast<R*>(smem_raw + HOFF);
+    R* Nb = reinterpret_cast<R*>(smem_raw + NOFF);
+    R* Out = reinterpret_cast<R*>(smem_raw + OOFF);
+    // the thread's point: box index, output slot, whether it is in the N range
+    int pi, po;
+    bool pN;
+    {
+        const int w = tid >> 5, lane = tid & 31;
+        int lx = 4 + lane, ly = w;
+        bool has = true;
+        if (w >= AH) {
+            const int e = lane + 32 * (w - AH);
+            has = e < NE;
+            if (e < PY + 2) {
+                lx = 2;
+                ly = 1 + e;
+            } else if (e < 2 * PY + 5) {
+                lx = 3;
+                ly = e - (PY + 2);
+            } else {
+                lx = PX + 4;
+                ly = e - (2 * PY + 5);
+            }
+        }
+        pi = has ? lx + BX * ly : -1;
+        pN = has && lx >= 3 && ly >= 1;
+        po = (has && lx >= 4 && lx < PX + 4 && ly >= 2 && ly < PY + 2) ? (lx - 4) + PX * (ly - 2) : -1;
+    }
+    auto fetch = [&]() {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        return it;
+    };
+    int acq_sim = -1;         // thread 0: the simulation whose tensor maps it has acquired
+    auto issue = [&](int it, int b) {
+        if (tid != 0) return;
+        const Work w = work[it];
+        const SimDev& S = ONE ? one : sims[w.sim];
+        const int t = w.tile;
+        const int o[3] = {(t % S.nyt[0]) * PX - 4 + GX, (t / S.nyt[0]) * PY - 2 + G, 0};
+        const int p = S.st->parity;
+        if (!ONE && w.sim != acq_sim) {
+            tensormap_acquire(&S.tm_yin);
+            tensormap_acquire(&S.tm_yj);
+            tensormap_acquire(&S.tm_yout);
+            acq_sim = w.sim;
+        }
+        unsigned char* box = smem_raw + b * BOXB;
+        mbar_arrive_expect_tx(&bars[b], (unsigned)(9 * BV * sizeof(R)));
+        tma_load_box<2>(box, &S.tm_yin, o, comp_eb(p), &bars[b]);
+        tma_load_box<2>(box + JOFF, &S.tm_yj, o, comp_j(p), &bars[b]);
+    };
+    int item = fetch();
+    if (item < nwork) issue(item, 0);
+    int buf = 0;
+    while (item < nwork) {
+        const int next = fetch();
+        if (next < nwork) issue(next, buf ^ 1);
+        const R* I0 = reinterpret_cast<const R*>(smem_raw + buf * BOXB);           // Ex Ey Ez Bx By Bz
+        const R* J0 = reinterpret_cast<const R*>(smem_raw + buf * BOXB + JOFF);    // Jx Jy Jz
+        const Work wk = work[item];
+        const SimDev& S = ONE ? one : sims[wk.sim];
+        DevState* st = S.st;
+        const int par = st->parity;
+        const int n0 = S.n[0], n1 = S.n[1];
+        const int x0 = (wk.tile % S.nyt[0]) * PX, y0 = (wk.tile / S.nyt[0]) * PY;
+        const bool interior = x0 > 0 && x0 + PX < n0 && y0 > 0 && y0 + PY < n1;
+        const bool xend = x0 + PX == n0, yend = y0 + PY == n1;
+        const YeeC<R>& yc = yee_of<R>(S);
+        const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
+        // the point's faces and validity (bits as in the 3D kernel), and whether it is an
+        // output on the node line past the tile
+        unsigned f = 0;
+        if (pi >= 0) {
+            const int gx = x0 - 4 + pi % BX, gy = y0 - 2 + pi / BX;
+            const bool past = (xend && gx == n0 && gy >= y0 && gy <= y0 + PY - (yend ? 0 : 1)) ||
+                              (yend && gy == n1 && gx >= x0 && gx <= x0 + PX - (xend ? 0 : 1));
+            f = (gx == 0 || gx == n0 ? 1u : 0u) | (gy == 0 || gy == n1 ? 2u : 0u) |
+                (gx >= 0 && gx <= n0 - 1 ? 4u : 0u) | (gx >= 0 && gx <= n0 ? 8u : 0u) |
+                (gy >= 0 && gy <= n1 - 1 ? 16u : 0u) | (gy >= 0 && gy <= n1 ? 32u : 0u) |
+                (gx == 0 ? 64u : 0u) | (gy == 0 ? 128u : 0u) | (past ? 256u : 0u);
+        }
+        const bool ok = mbar_wait_bounded(&bars[buf], (phases >> buf) & 1u);
+        phases ^= 1u << buf;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&st->status, (unsigned)FLAG_TIMEOUT);
+                // let the loads still in flight (this tile's, and the next one's) land
+                if (!ok) mbar_wait_bounded(&bars[buf], ((phases >> buf) & 1u) ^ 1u);
+                if (next < nwork) mbar_wait_bounded(&bars[buf ^ 1], (phases >> (buf ^ 1)) & 1u);
+                bulk_wait0();
+            }
+            return;
+        }
+        // A: B^{n+1/2} on the Bh range
+        if (pi >= 0) {
+            const int i = pi;
+            const R dEz_dy = I0[2 * BV + i + BX] - I0[2 * BV + i];
+            const R dEx_dy = I0[i + BX] - I0[i];
+            const R dEz_dx = I0[2 * BV + i + 1] - I0[2 * BV + i];
+            const R dEy_dx = I0[BV + i + 1] - I0[BV + i];
+            Hb[i] = I0[3 * BV + i] - hc * (dEz_dy - R(0));
+            Hb[BV + i] = I0[4 * BV + i] - hc * (R(0) - dEz_dx);
+            Hb[2 * BV + i] = I0[5 * BV + i] - hc * (dEy_dx - dEx_dy);
+        }
+        __syncthreads();
+        // B: E^{n+1} on the N range, the Mur condition on the faces
+        if (pN) {
+            const int i = pi;
+            auto enew = [&](int c, int j) -> R {
+                if (c == 0) return I0[j] + cdt * ((Hb[2 * BV + j] - Hb[2 * BV + j - BX]) - R(0)) - dt * J0[j];
+                if (c == 1) return I0[BV + j] + cdt * (R(0) - (Hb[2 * BV + j] - Hb[2 * BV + j - 1])) - dt * J0[BV + j];
+                return I0[2 * BV + j] + cdt * ((Hb[BV + j] - Hb[BV + j - 1]) - (Hb[j] - Hb[j - BX])) - dt * J0[2 * BV + j];
+            };
+            auto mur = [&](int c, int j, int nb, R en_nb) -> R { return I0[c * BV + nb] + km * (en_nb - I0[c * BV + j]); };
+            const bool fx = f & 1u, fy = f & 2u;
+            if (interior || (!fx && !fy)) {
+                Nb[i] = enew(0, i);
+                Nb[BV + i] = enew(1, i);
+                Nb[2 * BV + i] = enew(2, i);
+            } else {
+                const int sx = (f & 64u) ? 1 : -1, sy = (f & 128u) ? BX : -BX;
+                Nb[i] = fy ? mur(0, i, i + sy, enew(0, i + sy)) : enew(0, i);
+                Nb[BV + i] = fx ? mur(1, i, i + sx, enew(1, i + sx)) : enew(1, i);
+                R vz;
+                if (fx && fy) {
+                    const int nb = i + sx;
+                    vz = mur(2, i, nb, mur(2, nb, nb + sy, enew(2, nb + sy)));
+                } else if (fx) {
+                    vz = mur(2, i, i + sx, enew(2, i + sx));
+                } else {
+                    vz = mur(2, i, i + sy, enew(2, i + sy));
+                }
+                Nb[2 * BV + i] = vz;
+            }
+        }
+        // the previous tile's store has read the output buffer that D rewrites
+        if (tid == 0) bulk_wait_read0();
+        __syncthreads();
+        // D: E^{n+1}, B^{n+1} on the tile (and the node line past it)
+        if (pi >= 0 && (po >= 0 || (f & 256u))) {
+            const int i = pi;
+            const R dNz_dy = Nb[2 * BV + i + BX] - Nb[2 * BV + i];
+            const R dNx_dy = Nb[i + BX] - Nb[i];
+            const R dNz_dx = Nb[2 * BV + i + 1] - Nb[2 * BV + i];
+            const R dNy_dx = Nb[BV + i + 1] - Nb[BV + i];
+            R v[6] = {Nb[i], Nb[BV + i], Nb[2 * BV + i], Hb[i] - hc * (dNz_dy - R(0)),
+                      Hb[BV + i] - hc * (R(0) - dNz_dx), Hb[2 * BV + i] - hc * (dNy_dx - dNx_dy)};
+            if (!interior) {
+                const bool xs = f & 4u, xn = f & 8u, ys = f & 16u, yn = f & 32u;
+                if (!(xs && yn)) v[0] = R(0);
+                if (!(xn && ys)) v[1] = R(0);
+                if (!(xn && yn)) v[2] = R(0);
+                if (!(xn && ys)) v[3] = R(0);
+                if (!(xs && yn)) v[4] = R(0);
+                if (!(xs && ys)) v[5] = R(0);
+            }
+            const int gx = x0 - 4 + i % BX, gy = y0 - 2 + i / BX;
+            R* jp = reinterpret_cast<R*>(S.F) + (long long)comp_j(1 - par) * S.sc + (long long)(gy + G) * S.sy + (gx + GX);
+            if (po >= 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) Out[c * TV + po] = v[c];
+            } else {
+                R* ep = jp + (long long)(comp_eb(1 - par) - comp_j(1 - par)) * S.sc;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) ep[c * S.sc] = v[c];
+            }
+            // clear J_{1-p} (the next step deposits into it)
+            jp[0] = R(0);
+            jp[S.sc] = R(0);
+            jp[2 * S.sc] = R(0);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            const int oc[3] = {x0 + GX, y0 + G, 0};
+            tma_store_box<2>(&S.tm_yout, oc, comp_eb(1 - par), Out);
+            bulk_commit();
+        }
+        // this box buffer takes the tile after next: its reads above are behind the barrier
+        item = next;
+        buf ^= 1;
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+template <typename R, int PY, int NT>
+__global__ void __launch_bounds__(NT, 2) k_yee2r(const SimDev* __restrict__ sims, const Work* __restrict__ work,
+                                                 int nwork, int* __restrict__ counter)
+{
+    yee2r_body<R, PY, NT, false>(sims, *sims, work, nwork, counter);
+}
+
+template <typename R, int PY, int NT>
+__global__ void __launch_bounds__(NT, 2) k_yee2r1(const __grid_constant__ SimDev one, const Work* __restrict__ work,
+                                                  int nwork, int* __restrict__ counter)
+{
+    yee2r_body<R, PY, NT, true>(nullptr, one, work, nwork, counter);
 }
 
 // ---------------------------------------------------------------------------------
@@ -731,16 +975,12 @@ __global__ void __launch_bounds__(NT) k_yee3s1(const __grid_constant__ SimDev on
     yee3s_body<R, PX, PY, NS, NT, true>(nullptr, one, work, nwork, counter);
 }
 
-// 1D/2D field-solver tiles (must match the host's tile choice)
+// 1D field-solver tiles (must match the host's tile choice)
 template <int D>
 struct YeeTile;
 template <>
 struct YeeTile<1> {
     static constexpr int X = 128, Y = 1, Z = 1;
-};
-template <>
-struct YeeTile<2> {
-    static constexpr int X = 32, Y = 16, Z = 1;
 };
 
 template <int D, typename R>
@@ -753,6 +993,11 @@ static void yee_t(const Group& g, cudaStream_t s)
         else
             k_yee3s<R, Y3_PX, Y3_PY, Y3_NS, Y3_NT>
                 <<<g.yee_grid, Y3_NT, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
+    } else if constexpr (D == 2) {
+        if (g.one)
+            k_yee2r1<R, Y2_PY, Y2_NT><<<g.yee_grid, Y2_NT, g.yee_smem, s>>>(*g.one, g.ywork, g.nywork, g.counters + 2);
+        else
+            k_yee2r<R, Y2_PY, Y2_NT><<<g.yee_grid, Y2_NT, g.yee_smem, s>>>(g.sims, g.ywork, g.nywork, g.counters + 2);
     } else {
         if (g.one)
             k_yee1<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>
@@ -776,6 +1021,15 @@ static void attr_yee(size_t smem, int* out)
         cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, Y3_NT, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k1, Y3_NT, smem);
+        *out = std::min(*out, b1);
+    } else if constexpr (D == 2) {
+        auto k = k_yee2r<R, Y2_PY, Y2_NT>;
+        auto k1 = k_yee2r1<R, Y2_PY, Y2_NT>;
+        int b1 = 0;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, Y2_NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k1, Y2_NT, smem);
         *out = std::min(*out, b1);
     } else {
         auto k = k_yee<D, R, YeeTile<D>::X, YeeTile<D>::Y, YeeTile<D>::Z>;
