@@ -201,7 +201,9 @@ pic_status pic_init(const pic_config* cfg, const pic_allocator* alloc, void* str
  * that takes at most 1500 steps (electrons heated by the pulse, as in the run) and else by
  * moving the clock, so that the incident field and the deposit do their full work; the
  * candidate's time is the mean of the two.  It then destroys it; one
- * candidate holds device memory at a time.  Candidates that do not fit (shared memory,
+ * candidate holds device memory at a time.  The tiles are timed at work items of 4096 for a
+ * run of at least 16 such work items per SM and of 2048 otherwise; a later candidate must be
+ * faster by more than 1 % to be chosen.  Candidates that do not fit (shared memory,
  * device memory) are skipped.  On success cfg->tile and cfg->chunk hold the fastest
  * choice and *ms_per_step (may be NULL) its time per step.  Only tile/chunk entries left
  * at 0 are tuned.  Results are cached for the process per (dim, precision, n, ppc, beam,
