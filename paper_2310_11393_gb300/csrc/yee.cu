@@ -583,9 +583,10 @@ __global__ void __launch_bounds__(NT, 2) k_yee2r1(const __grid_constant__ SimDev
 //         by one TMA store (double-buffered) and J_{1-p} of plane k is cleared; a column
 //         that ends at x = n_x (y = n_y) also writes that node plane with plain stores,
 // iteration q runs A(q+1) together with D(q-1), then B(q+1): two barriers per plane.
-// Bh is kept for x in [x0-2, x0+PX], y in [y0-2, y0+PY]; N for x in [x0-1, x0+PX],
-// y in [y0-1, y0+PY] and planes from z0-1: one more than the outputs need on the low
-// side, so that every face point's Mur neighbour (one point inwards) is on hand.
+// Bh is kept for x in [x0-2, x0+PX], y in [y0-2, y0+PY] and planes from z0-1; N for x in
+// [x0-1, x0+PX], y in [y0-1, y0+PY] and planes from z0: one more point than the outputs need
+// on the low side in x and y, so that every face point's Mur neighbour (one point inwards)
+// is on hand.
 // ---------------------------------------------------------------------------------
 template <typename R, int PX, int PY, int NS, int NT, bool ONE>
 __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, const SimDev& one,
@@ -668,7 +669,8 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
         const int x0 = cx * PX, y0 = cy * PY;
         const int z0 = cz * S.yt[2];
         const int z1 = min(z0 + S.yt[2], n2 + 1);
-        const int pa = z0 - 2, plast = z1 + 1;     // planes loaded
+        // planes loaded: from z0-1 (Bh(z0-1) enters N(z0)) to z1+1 (E(z1+1) enters Bh(z1))
+        const int pa = z0 - 1, plast = z1 + 1;
         const bool col_int = x0 > 0 && x0 + PX < n0 && y0 > 0 && y0 + PY < n1;
         const YeeC<R>& yc = yee_of<R>(S);
         const R cdt = yc.cdt, hc = yc.hc, dt = yc.dt, km = yc.km;
@@ -767,7 +769,7 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
 
 
         bool failed = false;
-        for (int q = z0 - 3; q <= z1; ++q) {
+        for (int q = z0 - 2; q <= z1; ++q) {
             // Plane q was last read in the previous iteration unless this one's z-face passes
             // read it (B(n_z) reads E(n_z - 1), the plane-0 faces E(0)): otherwise its stage
             // takes plane q+NS as soon as this iteration's first barrier has passed
@@ -866,7 +868,7 @@ __device__ __forceinline__ void yee3s_body(const SimDev* __restrict__ sims, cons
             // S2: B(q+1) on the thread's points of the N range, with the Mur condition on the
             // x and y faces; on the z faces the passes of mur_plane follow
             const int b = q + 1;
-            if (b >= z0 - 1 && b <= z1) {
+            if (b >= z0 && b <= z1) {
                 const bool fz = b == 0 || b == n2;
                 const bool faces = !col_int || fz;
                 const R* I0 = In(stage_of(b));
