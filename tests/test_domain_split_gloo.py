@@ -2,9 +2,9 @@
 two and three gloo ranks on the CPU, each rank stepping its slab with the oracle's two
 step phases, against the unsplit oracle run element by element: every electron's position
 and momentum by id, the exits, and all nine field components (E, B and the last step's J)
-at every grid point.  The run is chosen so that electrons cross the cuts and their
-currents straddle them (a tightly focused LP pulse at a0 = 10 through a slab the cuts run
-through).  Only the summation order of J at points next to a cut differs from the unsplit
+at every grid point.  The runs are chosen so that electrons cross the cuts and their
+currents straddle them (a tightly focused LP pulse at a0 = 10 through a 2D slab, an RP pulse
+at a0 = 10 through a 3D slab, the cuts running through both).  Only the summation order of J at points next to a cut differs from the unsplit
 run (contributions from both sides), so the bar is FP64 round-off."""
 import math
 import os
@@ -23,9 +23,18 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _workload():
+def _workload(dim=2):
     import synth
 
+    if dim == 3:
+        # a tightly focused RP pulse through a 3D slab the cuts run through
+        n = (48, 14, 14)
+        dx = 2 * math.pi / 16
+        dt = 0.95 * dx / math.sqrt(3)
+        return synth.Workload(name="3d_rp_split", dim=3, n=n, dx=dx, steps=30, beam=synth.BEAM_RP, a0=10.0,
+                              duration=synth.fs(5.0), w0=2 * math.pi * 0.7, slab_lo=(8, 3, 3), slab_hi=(40, 11, 11),
+                              n_e=0.05, ppc=1, seed=43, focus=(24 * dx, 7 * dx, 7 * dx), t_focus=15 * dt,
+                              precision=synth.FP64)
     n = (96, 40, 1)
     dx = 2 * math.pi / 32
     dt = 0.95 * dx / math.sqrt(2)
@@ -60,7 +69,7 @@ class OracleSlab:
         self.s.set_particles(x, u, w, ids)
 
 
-def _rank(rank, world, port, steps, q):
+def _rank(rank, world, port, steps, q, dim):
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
 
@@ -71,12 +80,12 @@ def _rank(rank, world, port, steps, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = _workload()
+    w = _workload(dim)
     slabs = domain.decompose(w.n[0], world)
     me = slabs[rank]
     sh = domain.shift_of(me, w.dx)
     # the slab's own box: the global workload moved by -shift along x, electrons set explicitly
-    lw = w.with_(n=(me.n_local, w.n[1], 1), focus=(w.focus[0] - sh, w.focus[1], 0.0), ppc=0)
+    lw = w.with_(n=(me.n_local, w.n[1], w.n[2]), focus=(w.focus[0] - sh, w.focus[1], w.focus[2]), ppc=0)
     cfg = oracle.config_from(lw)
     gcfg = oracle.config_from(w)
     cfg.a, cfg.s, cfg.psi0 = gcfg.a, gcfg.s, gcfg.psi0          # the global pulse parameters
@@ -93,13 +102,13 @@ def _rank(rank, world, port, steps, q):
     dist.destroy_process_group()
 
 
-def _split_run(world, steps):
+def _split_run(world, steps, dim=2):
     import torch.multiprocessing as mp
 
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, steps, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, steps, q, dim)) for r in range(world)]
     for p in procs:
         p.start()
     out = sorted([q.get(timeout=600) for _ in procs], key=lambda t: t[0])
@@ -109,16 +118,16 @@ def _split_run(world, steps):
     return out
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_split_run_equals_the_unsplit_run(orc, world):
+@pytest.mark.parametrize("dim,world", [(2, 2), (2, 3), (3, 2)])
+def test_split_run_equals_the_unsplit_run(orc, dim, world):
     import synth
     from paper_2310_11393_gb300 import domain
 
-    w = _workload()
+    w = _workload(dim)
     steps = w.steps
     ref = orc.Sim(orc.config_from(w))
     ref.step(steps)
-    out = _split_run(world, steps)
+    out = _split_run(world, steps, dim)
     # electrons: the union over the ranks is the unsplit set, value by value
     parts = {k: np.concatenate([o[1][k] for o in out]) for k in ("x", "u", "w", "id")}
     pr = ref.particles()
