@@ -1,7 +1,8 @@
-"""The benchmark's push count (host logic, CPU): every electron alive at the end of the timed
-steps counts each of them, one that left the box counts the timed steps up to the one in
-which it left (its exit record holds that step's index).  Checked on a fake simulation and on
-the oracle, whose per-step particle count gives the same sum step by step."""
+"""The benchmark's host logic (CPU).  Its push count: every electron alive at the end of the
+timed steps counts each of them, one that left the box counts the timed steps up to the one
+in which it left (its exit record holds that step's index); checked on a fake simulation and
+on the oracle, whose per-step particle count gives the same sum step by step.  Its timed
+window: centred on the pulse's crossing of the focus."""
 import math
 import os
 import sys
@@ -61,3 +62,19 @@ def test_exit_record_count_matches_the_stepwise_sum_on_the_oracle(orc):
     assert len(inside) > 2 and len(np.unique(inside)) > 1   # exits spread over the window
     counted = float(sim.num_particles()) * steps + float(np.sum(inside - s0 + 1))
     assert counted == stepwise
+
+
+def test_focus_window_of_the_benchmark_workloads():
+    """The timed window is centred on the step at which the pulse peak crosses the focus
+    and kept inside the run: 3D RP steps 457-477, 2D LP 752-772 (the windows the profiles
+    and the measurements name)."""
+    import bench
+    import synth
+
+    w3, w2 = synth.c3_3d_rp(), synth.c2_2d_lp()
+    assert bench.window_start(w3, 20, "focus") == 457
+    assert bench.window_start(w2, 20, "focus") == 752
+    assert bench.window_start(w3, 20, "start") == 0
+    assert bench.window_start(w3, w3.steps, "focus") == 0          # K covers the run
+    k = w3.steps - 10                                                # kept inside the run
+    assert bench.window_start(w3, k, "focus") + k <= w3.steps
